@@ -1,0 +1,24 @@
+"""FP64 CPU checker for the bilevel hypergradient path (test infrastructure).
+
+Plain, slow NumPy/SciPy code written from the paper (Ehrhardt, Gazzola,
+Scott, "Efficient gradient-based methods for bilevel learning via recycling
+Krylov subspaces"), used only by the tests, by ``__graft_entry__.smoke()``
+and by the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py``.
+The product path never imports it, and it imports nothing from the product
+except the seeded input generator ``paper_2412_08264_gb300.synth`` (which
+holds no arithmetic of the method).
+
+Modules
+  operators   blur A, correlation filters K_j, forward differences D (Section 5)
+  functional  lower-level Phi, gradient, Hessian action, J w (eqs. (1.1), (2.4)-(2.7), (5.1))
+  krylov      CG, recycled CG, MINRES, RMINRES (Section 2.2, Algorithm 3, Appendix A)
+  recycle     Ritz, harmonic Ritz, Ritz generalized singular vectors, NSC (Sections 3, 4)
+  lbfgs       lower-level L-BFGS with backtracking (Section 5.1)
+  bilevel     hypergradient, gradient descent with Armijo backtracking (Algorithms 1, 2), Adam
+
+Parity status: every function is pinned by a test under tests/ against a
+property fixed by the mathematics (adjoint identities, finite differences,
+dense assembly, closed forms, textbook special cases).  Iteration counts of
+the paper's own experiments are not reproducible (its datasets and figures
+are absent): parity unpinned for those counts.
+"""
