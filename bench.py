@@ -1,0 +1,370 @@
+"""Throughput of the hypergradient hot path on the 64-pair batch workload.
+
+One step = one outer iteration over the batch (64 training pairs of uneven sizes, FoE with
+16 5x5 filters): warm-started lower solve (L-BFGS), recycle refresh, warm-started recycled-CG
+Hessian solve, J w contraction, then an Adam update of theta (Section 5.2).  The metric is
+hypergradients per second at a stopping tolerance that keeps every hypergradient within 1e-4
+relative error of a tight reference solve (checked after the timed region and reported).
+
+Arms
+  default            the CUDA path (libbl), recycled CG with the chosen strategy; the same run
+                     also times plain warm-started CG on the same sequence.
+  --impl reference   the FP64 CPU checker on a bounded sample of the workload (host cores).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank solves its own batch (weak scaling) and the mean
+hypergradient is all-reduced once per step before the shared theta update.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+S_RECYCLE = 16
+MAX_BASIS = 64
+RTOL = 1e-4            # residual stopping tolerance (relative to ||g||)
+LOWER_GTOL = 1e-5      # lower-level gradient tolerance (relative to ||grad Phi(0)||)
+ADAM_LR = 1e-2
+FP32_FMA_LANES = 152 * 128   # GB300: 152 SMs x 128 FP32 lanes
+
+
+def hvp_flops_per_pixel(n_filters, f, rb):
+    """Algorithmic FP32 flops of one Hessian action per pixel (fields variant):
+    per filter K v (2 T), times d_j (1), K^T (2 T); blur A A v separable (4 passes x (2 r_b + 1)
+    FMA = 8 (2 r_b + 1) flop); l2 term and sum (2)."""
+    T = f * f
+    return n_filters * (4 * T + 1) + 8 * (2 * rb + 1) + 2
+
+
+def hvp_bytes_per_pixel(n_filters, esz=4):
+    """Algorithmic HBM bytes of one Hessian action per pixel: v in, H v out, N fields d_j in."""
+    return (2 + n_filters) * esz
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU arm
+
+def gpu_arm(args, rank, world, dist):
+    import torch
+    from paper_2412_08264_gb300 import api, synth
+    from paper_2412_08264_gb300.strategy import parse
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    wl = synth.batch_64(replica=rank)
+    K = len(wl.pairs)
+    xs_h = torch.tensor(np.concatenate([x.ravel() for x in wl.x_star]), dtype=torch.float32).pin_memory()
+    nz_h = torch.tensor(np.concatenate([x.ravel() for x in wl.noise]), dtype=torch.float32).pin_memory()
+    xs = xs_h.to(dev)
+    P0 = api.from_workload(wl, xs, xs)
+    y = P0.forward(xs) + nz_h.to(dev)
+    del P0
+    y_h = y.cpu().pin_memory()
+    n_pix = xs.numel()
+    strategy = parse(args.strategy)
+
+    def run(strat, steps, warmup, e2e=False, validate=False):
+        P = api.from_workload(wl, y, xs, max_recycle=S_RECYCLE, max_basis=MAX_BASIS)
+        y_d = torch.empty_like(y)
+        xs_d = torch.empty_like(xs)
+        theta = wl.theta0.copy()
+        theta_d = torch.tensor(theta, dtype=torch.float64, device=dev)
+        m = np.zeros_like(theta)
+        v2 = np.zeros_like(theta)
+        xhat = P.zeros()
+        w = P.zeros()
+        stream = torch.cuda.current_stream(dev)
+        iters = []
+        hg_prev = None
+        state = {"t": 0}
+
+        def step(i, record):
+            nonlocal theta, m, v2, hg_prev
+            if e2e:
+                y_d.copy_(y_h, non_blocking=True)
+                xs_d.copy_(xs_h, non_blocking=True)
+                P.set_data(y_d, xs_d)
+            P.lower_solve(theta_d, xhat, gtol=LOWER_GTOL, relative=True, max_iters=2000, allow_noconv=True)
+            if strat.recycles and state["t"] > 0:
+                P.ritz_update(strat, S_RECYCLE)
+            info = P.hessian_solve(w, recycle=strat.recycles, nsc=strat.nsc, tol=RTOL, relative=True, maxit=3000,
+                                   store_basis=strat.recycles, warm_start=True,
+                                   nsc_scale=None if hg_prev is None else [hg_prev] * K, allow_noconv=True)
+            mean, per = P.hypergrad(w, per_pair=True)
+            if world > 1:
+                dist.all_reduce(mean)
+                mean /= world
+            g = mean.cpu().numpy()                       # the step's result, read back every step
+            hg_prev = float(np.linalg.norm(g))
+            # Adam (Section 5.2: fixed step length 1e-2)
+            state["t"] += 1
+            t = state["t"]
+            m = 0.9 * m + 0.1 * g
+            v2 = 0.999 * v2 + 0.001 * g * g
+            theta = theta - ADAM_LR * (m / (1 - 0.9 ** t)) / (np.sqrt(v2 / (1 - 0.999 ** t)) + 1e-8)
+            theta_d.copy_(torch.from_numpy(theta), non_blocking=False)
+            if record:
+                iters.append([d["iters"] for d in info])
+            return per
+
+        for i in range(warmup):
+            step(i, False)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        clocks = Clocks(dev.index)
+        clocks.start()
+        P.profile(True)
+        launches0 = P.launch_count()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        per = None
+        for i in range(steps):
+            per = step(i, True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms = ev0.elapsed_time(ev1)
+        prof = P.profile_read()
+        P.profile(False)
+        launches = P.launch_count() - launches0
+        ck = clocks.stop()
+        res = dict(ms=ms, iters=iters, prof=prof, launches=launches, clocks=ck)
+        if validate:
+            # tight reference at the last step's point: plain CG to rtol 1e-7 from the computed w
+            wref = w.clone()
+            P.hessian_solve(wref, recycle=False, tol=1e-7, relative=True, maxit=6000, store_basis=False,
+                            warm_start=True, allow_noconv=True)
+            _, per_ref = P.hypergrad(wref, per_pair=True)
+            err = (per - per_ref).norm(dim=1) / per_ref.norm(dim=1)
+            mean_err = float((per.mean(0) - per_ref.mean(0)).norm() / per_ref.mean(0).norm())
+            res["hg_err_max"] = float(err.max())
+            res["hg_err_mean_grad"] = mean_err
+        del P
+        return res
+
+    rec = run(strategy, args.steps, args.warmup, validate=True)
+    cg = run(parse("none"), args.steps, args.warmup, validate=True) if (args.compare_cg and strategy.recycles) else None
+    e2e = run(strategy, args.steps, args.warmup, e2e=True) if args.e2e else None
+    return dict(rec=rec, cg=cg, e2e=e2e, K=K, n_pix=n_pix, wl=wl, strategy=strategy)
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU checker arm (bounded sample)
+
+def oracle_sample(steps, warmup, max_seconds=None, strategy="RGen-L(R)"):
+    """Run the FP64 checker on one 128x128 pair of the batch for warmup + steps outer steps.
+    Returns (seconds per timed step, sample description)."""
+    from paper_2412_08264_gb300 import synth
+    from paper_2412_08264_gb300.strategy import parse
+    from oracle.bilevel import BilevelProblem, Adam
+    from oracle.krylov import rcg
+    from oracle.recycle import refresh
+
+    wl = synth.batch_64()
+    k0 = min(range(len(wl.pairs)), key=lambda k: wl.pairs[k].height * wl.pairs[k].width)
+    wl.pairs, wl.x_star, wl.noise = [wl.pairs[k0]], [wl.x_star[k0]], [wl.noise[k0]]
+    prob = BilevelProblem(wl)
+    st = parse(strategy)
+    ll = prob.lowers[0]
+    theta = wl.theta0.copy()
+    opt = Adam(ADAM_LR)
+    x = np.zeros((ll.h, ll.w))
+    w = np.zeros(ll.n)
+    U = C = V = None
+    times = []
+    g0 = np.linalg.norm(ll.grad(np.zeros_like(x), theta))
+    for i in range(warmup + steps):
+        t0 = time.perf_counter()
+        xs, _ = prob.solve_lower(theta, [x], gtol=LOWER_GTOL * g0)
+        x = xs[0]
+        AH = prob.apply_H(0, x, theta)
+        if st.recycles and V is not None:
+            Up = U if U is not None else np.zeros((ll.n, 0))
+            U, C, Z, _ = refresh(Up, V, AH, lambda v: prob.Jw(0, x, theta, v), S_RECYCLE, st.kind, st.size, st.side)
+        g = prob.rhs(0, x)
+        out = rcg(AH, g, w, U, C, tol=RTOL * np.linalg.norm(g), maxit=3000, kmax_store=MAX_BASIS)
+        w, V = out["w"], out["V"]
+        hg = prob.Jw(0, x, theta, w)
+        theta = opt.step(theta, hg)
+        dt = time.perf_counter() - t0
+        if i >= warmup:
+            times.append(dt)
+        if max_seconds is not None and sum(times) > max_seconds and len(times) >= 1:
+            break
+    desc = (f"pair {k0} of the 64-pair batch ({ll.h}x{ll.w}, 16 5x5 filters), {strategy}, "
+            f"{warmup} warm-up + {len(times)} timed outer steps, FP64 NumPy")
+    return float(np.mean(times)), len(times), desc
+
+
+# ---------------------------------------------------------------------------------------------
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--strategy", default="RGen-L(R)")
+    ap.add_argument("--no-compare-cg", dest="compare_cg", action="store_false")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    metric = "hypergradients/s at 1e-4 rel. error (batched RCG vs plain CG); HVP HBM GB/s"
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        sec, n, desc = oracle_sample(args.steps, args.warmup, strategy=args.strategy)
+        v = 1.0 / sec
+        print(json.dumps({"impl": "reference", "metric": metric, "value": v, "unit": "hypergradients/s",
+                          "n_gpus": args.gpus, "steps": n, "warmup": args.warmup, "ms_per_step": sec * 1e3,
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                          "data": "synthetic",
+                          "config": {"workload": "batch64_foe_n16f5 (sample)", "strategy": args.strategy},
+                          "cpu_baseline": {"value": v, "unit": "hypergradients/s", "cores": os.cpu_count(),
+                                           "kind": "oracle", "sample": desc},
+                          "e2e": {"value": v, "unit": "hypergradients/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return
+
+    import torch
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+        dist = tdist
+    out = gpu_arm(args, rank, world, dist)
+    rec, cg = out["rec"], out["cg"]
+    K, n_pix, wl = out["K"], out["n_pix"], out["wl"]
+
+    def tmax(ms):
+        if world == 1:
+            return ms
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ms = tmax(rec["ms"])
+    value = K * world * args.steps / (ms / 1e3)
+    # roofline of the dominant kernel: the fused Hessian action of the Krylov loop
+    hv = rec["prof"]["hvp"]
+    fpp = hvp_flops_per_pixel(wl.n_filters, wl.filter_size, wl.pairs[0].blur_radius)
+    bpp = hvp_bytes_per_pixel(wl.n_filters)
+    avg_ms = hv["ms"] / max(1, hv["launches"])
+    flops_per_launch = fpp * hv["pixels"] / max(1, hv["launches"])
+    achieved_tflops = flops_per_launch / (avg_ms / 1e3) / 1e12
+    ck = rec["clocks"] or {}
+    peak_tflops = FP32_FMA_LANES * 2 * 2070e6 / 1e12
+    gbs = bpp * hv["pixels"] / max(1, hv["launches"]) / (avg_ms / 1e3) / 1e9
+    total_prof = sum(v["ms"] for v in rec["prof"].values())
+    line = {
+        "metric": metric, "value": value, "unit": "hypergradients/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"batch64_foe_n16f5: {K} pairs, sides 128-512, {n_pix} px, 16 5x5 filters, "
+                               f"9x9 blur, p={wl.n_params}",
+                   "strategy": out["strategy"].acronym(), "recycle_dim": S_RECYCLE, "max_basis": MAX_BASIS,
+                   "stop": f"residual rtol {RTOL}", "lower_gtol_rel": LOWER_GTOL, "outer": "Adam lr 1e-2",
+                   "l2": "inputs larger than L2 (batch working set > 1 GB), no flush"},
+        "hg_rel_err_max": rec.get("hg_err_max"), "hg_rel_err_mean_grad": rec.get("hg_err_mean_grad"),
+        "krylov_iters_per_step": [int(np.max(it)) for it in rec["iters"]],
+        "krylov_iters_total": int(np.sum(rec["iters"])),
+        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / peak_tflops, "traffic": None,
+                     "kernel": "k_foe_stencil<float,5,HVP> (fused blur + FoE Hessian action + dots)",
+                     "flops_per_pixel": fpp, "pixels_per_launch": hv["pixels"] / max(1, hv["launches"]),
+                     "avg_launch_ms": avg_ms, "hbm_gbs_algorithmic": gbs,
+                     "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                     "share_of_step": hv["ms"] / max(1e-9, rec["ms"])},
+        "kernel_ms": {k: round(v["ms"], 3) for k, v in rec["prof"].items()},
+        "gpu_launches": rec["launches"],
+        "clocks": ck,
+    }
+    if cg is not None:
+        ms_cg = tmax(cg["ms"])
+        line["plain_cg"] = {"value": K * world * args.steps / (ms_cg / 1e3), "ms_per_step": ms_cg / args.steps,
+                            "krylov_iters_total": int(np.sum(cg["iters"])), "hg_rel_err_max": cg.get("hg_err_max")}
+    if out["e2e"] is not None:
+        ms_e = tmax(out["e2e"]["ms"])
+        h2d = 2 * n_pix * 4 + wl.n_params * 8
+        line["e2e"] = {"value": K * world * args.steps / (ms_e / 1e3), "unit": "hypergradients/s",
+                       "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": wl.n_params * 8}
+    if rank == 0 and world == 1 and args.cpu_baseline:
+        sec, n, desc = oracle_sample(2, 1, max_seconds=30.0, strategy=args.strategy)
+        line["cpu_baseline"] = {"value": 1.0 / sec, "unit": "hypergradients/s", "cores": os.cpu_count(),
+                                "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

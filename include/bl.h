@@ -1,0 +1,247 @@
+/*
+ * bl.h -- C ABI of the GB300 bilevel-hypergradient library.
+ *
+ * One call sequence computes the hypergradient of a variational imaging
+ * problem for a batch of K training pairs (Ehrhardt, Gazzola, Scott,
+ * "Efficient gradient-based methods for bilevel learning via recycling
+ * Krylov subspaces"):
+ *
+ *   bl_problem_create   pairs (y_k, x*_k), blur A_k, regulariser R(x, theta)
+ *   bl_lower_solve      x^_k = argmin_x Phi_k(x, theta)          (eq. (1.1), (5.1); L-BFGS, Section 5.1)
+ *   bl_ritz_update      refresh U, C = H U from W = [U, V]       (Section 3, eq. (3.3) outer form)
+ *   bl_hessian_solve    H_k w_k = grad ell_k by recycled CG     (Section 2.2, eq. (2.5), Section 4 stopping)
+ *   bl_hypergrad        g_k = J_k w_k = -(D^2_{theta x} Phi_k)^T w_k   (eq. (2.7))
+ *
+ * Conventions shared by every entry point
+ *   - Images are H x W, row-major, pixel p = i * W + j, zero boundary.
+ *   - Scalar type of every image buffer is the problem's precision:
+ *     float for BL_FP32 (FP32 stencils, FP64 reductions and scalar recurrences),
+ *     double for BL_FP64.
+ *   - A "packed" buffer holds the images of the listed pairs back to back, in the
+ *     order of the `pairs` index array, each H_k * W_k elements.
+ *   - Device pointers are CUDA device memory owned by the caller unless stated;
+ *     the library reads them during the call's stream work and keeps no reference.
+ *   - theta (length p, double, device) is laid out per filter as
+ *     [alpha_1, taps_1 (f*f row-major, tap (a, b) at (a + r) * f + (b + r)), alpha_2, ...]
+ *     for the Fields-of-Experts regulariser (Section 5), p = N (f*f + 1); p = 1 for TV.
+ *   - All work is enqueued on the problem's stream.  Calls that return an info
+ *     array or host values synchronise that stream before returning.
+ *   - Errors: no exception crosses the ABI.  A call returns a bl_status; on any
+ *     status other than BL_OK / BL_ENOCONV, bl_last_error() gives a message
+ *     (thread-local, valid until the next call on the same thread).
+ */
+#ifndef BL_H_
+#define BL_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BL_MAX_FILTER_SIZE 7   /* f in {1, 3, 5, 7} */
+#define BL_MAX_BLUR_RADIUS 4   /* blur support (2 r_b + 1)^2, r_b <= 4 */
+
+typedef enum {
+  BL_OK = 0,
+  BL_EINVAL = 1,       /* invalid argument: null pointer, size, option out of range */
+  BL_ENOMEM = 2,       /* device allocation failed */
+  BL_ECUDA = 3,        /* a CUDA runtime call failed (message names it) */
+  BL_ENOCONV = 4,      /* a solve hit its iteration cap; results are still written */
+  BL_EBREAKDOWN = 5,   /* non-positive curvature or a non-finite value in a solve */
+  BL_ESTATE = 6        /* call out of order (e.g. solve before a point was set) */
+} bl_status;
+
+typedef enum { BL_REG_TV = 0, BL_REG_FOE = 1 } bl_reg_kind;
+typedef enum { BL_PHI_CHARBONNIER = 0, BL_PHI_SQ = 1, BL_PHI_LOG1P = 2 } bl_phi_kind;
+typedef enum { BL_FP32 = 0, BL_FP64 = 1 } bl_precision;
+
+/* One training pair: image size and its Gaussian blur A (Section 5.2):
+ * G[a, b] proportional to exp(-(a^2 + b^2) / (2 sigma^2)) on [-r_b, r_b]^2, summing to 1. */
+typedef struct {
+  int32_t height, width;
+  double blur_sigma;
+  int32_t blur_radius;
+} bl_pair_desc;
+
+/* Lower-level functional (eq. (1.1) with the eps term of eq. (5.1)):
+ *   Phi(x) = ||A x - y||^2 + R(x, theta) + (l2_eps / 2) ||x||^2
+ * FoE: R = sum_j exp(alpha_j) sum_p phi((k_j * x)[p]), (k * x)[p] = sum_o k[o] x[p + o].
+ * TV:  R = exp(theta_0) sum_p sqrt(|(D x)_p|^2 + phi_eps^2), forward differences. */
+typedef struct {
+  int32_t kind;          /* bl_reg_kind */
+  int32_t n_filters;     /* N (FoE) */
+  int32_t filter_size;   /* f, odd, <= BL_MAX_FILTER_SIZE (FoE) */
+  int32_t phi;           /* bl_phi_kind (FoE) */
+  double phi_eps;        /* Charbonnier / TV smoothing */
+  double l2_eps;         /* eps of eq. (5.1) */
+  int32_t precision;     /* bl_precision */
+  int32_t max_recycle;   /* largest recycle dimension s any later call may ask for */
+  int32_t max_basis;     /* Krylov vectors kept per solve for the next refresh (most recent) */
+} bl_reg_desc;
+
+typedef struct {
+  int32_t max_iters;     /* L-BFGS iteration cap */
+  int32_t history;       /* memory m (Section 5.1 uses 10), 1..16 */
+  double gtol;           /* stop when ||grad Phi|| <= gtol (absolute) ... */
+  int32_t gtol_relative; /* ... or, if non-zero, <= gtol * ||grad Phi(0)|| = gtol * ||2 A^T y|| */
+  int32_t max_backtrack; /* Armijo halvings per iteration */
+  double armijo_slack;   /* accept Phi(x + t d) <= Phi(x) + 1e-4 t g^T d + armijo_slack |Phi(x)|:
+                            0 is the plain Armijo rule; FP32 problems need about 1e-6 because FP32
+                            values of Phi cannot resolve decreases below that level */
+} bl_lbfgs_opts;
+
+typedef enum { BL_SOLVE_CG = 0, BL_SOLVE_RCG = 1 } bl_solve_method;
+typedef enum { BL_STOP_RESID = 0, BL_STOP_NSC = 1 } bl_stop_rule;
+
+typedef struct {
+  int32_t method;        /* BL_SOLVE_CG ignores the recycle space; BL_SOLVE_RCG uses it (if any) */
+  int32_t stop;          /* BL_STOP_RESID: ||r|| < tol * scale;
+                            BL_STOP_NSC: ||Z^T r|| < tol * scale (eq. (4.2)); falls back to the
+                            residual rule for a pair without a Ritz-GSV recycle space */
+  double tol;
+  int32_t relative;      /* RESID: scale = ||g_k|| if non-zero, else 1.
+                            NSC:   scale = nsc_scale[k] from bl_hessian_solve, else 1. */
+  int32_t maxit;
+  int32_t store_basis;   /* keep normalised residuals as V for the next bl_ritz_update */
+  int32_t warm_start;    /* non-zero: w (in) is the initial guess; zero: start from 0 */
+} bl_krylov_opts;
+
+typedef enum { BL_RECYCLE_RITZ = 0, BL_RECYCLE_HRITZ = 1, BL_RECYCLE_RGSV = 2 } bl_recycle_kind;
+typedef enum { BL_SIZE_SMALL = 0, BL_SIZE_LARGE = 1, BL_SIZE_MIXED = 2 } bl_recycle_size;
+typedef enum { BL_SIDE_RIGHT = 0, BL_SIDE_LEFT = 1, BL_SIDE_MIXED = 2 } bl_recycle_side;
+
+/* Table 1 grammar: Ritz-S = {RITZ, SMALL}, RGen-L(R) = {RGSV, LARGE, RIGHT}. */
+typedef struct {
+  int32_t kind;          /* bl_recycle_kind */
+  int32_t size;          /* bl_recycle_size */
+  int32_t side;          /* bl_recycle_side (RGSV only) */
+  int32_t s;             /* recycle dimension, 1..max_recycle; RGSV also needs s <= p */
+} bl_recycle_opts;
+
+typedef struct {
+  int32_t iters;         /* iterations taken */
+  int32_t status;        /* bl_status of this pair */
+  double resid;          /* final recursive residual norm ||r|| */
+  double nsc_est;        /* final ||Z^T r|| (0 without a Ritz-GSV space) */
+  double rhs_norm;       /* ||g|| */
+} bl_solve_info;
+
+typedef struct bl_problem bl_problem;
+
+/* Create a problem for K pairs (Section 5, eq. (5.2)).
+ * y_packed, xstar_packed: device, packed over pairs 0..K-1, precision's scalar type; copied.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream) that all later work runs on.
+ * Returns BL_EINVAL for K < 1, sizes < 1, filter size even or > 7, blur radius > 4,
+ * n_filters < 1 (FoE), unknown enum values or a null pointer. */
+bl_status bl_problem_create(const bl_pair_desc* pairs, int32_t K, const bl_reg_desc* reg,
+                            const void* y_packed, const void* xstar_packed, void* cuda_stream,
+                            bl_problem** out);
+void bl_problem_destroy(bl_problem* prob);
+bl_status bl_set_stream(bl_problem* prob, void* cuda_stream);
+
+/* Number of hyperparameters p and total pixels of the listed pairs (host values). */
+int32_t bl_num_params(const bl_problem* prob);
+int64_t bl_num_pixels(const bl_problem* prob, const int32_t* pairs, int32_t npairs);
+
+/* Replace the measurements and ground truths of the listed pairs (device, packed); same sizes as
+ * at creation.  The recycle state and the current point are kept. */
+bl_status bl_set_data(bl_problem* prob, const int32_t* pairs, int32_t npairs, const void* y_packed,
+                      const void* xstar_packed);
+
+/* y_k = A_k x_k for each listed pair (the blur of Section 5.2); x, out packed, device. */
+bl_status bl_forward(bl_problem* prob, const int32_t* pairs, int32_t npairs, const void* x_packed,
+                     void* out_packed);
+
+/* Set the point (theta, x^_k) at which H_k and J_k are evaluated (eqs. (2.6), (2.7)) and
+ * precompute the per-filter fields u_j = k_j * x^ and exp(alpha_j) phi''(u_j).
+ * theta: device, p doubles.  xhat_packed: device, packed over the listed pairs. */
+bl_status bl_set_point(bl_problem* prob, const int32_t* pairs, int32_t npairs,
+                       const double* theta, const void* xhat_packed);
+
+/* Lower-level solve by L-BFGS with Armijo backtracking (Section 5.1), warm-started from
+ * xhat_packed (in), result written back to xhat_packed (out), then bl_set_point.
+ * info: host array of npairs (iters = L-BFGS iterations, resid = final ||grad Phi||), or NULL.
+ * Returns BL_ENOCONV if a pair reached max_iters. */
+bl_status bl_lower_solve(bl_problem* prob, const int32_t* pairs, int32_t npairs, const double* theta,
+                         const bl_lbfgs_opts* opts, void* xhat_packed, bl_solve_info* info);
+
+/* Lower-level value and gradient at (x, theta) for the listed pairs (eq. (1.1), (5.1)):
+ * grad_packed (device, packed) receives grad Phi_k(x_k); values (device, npairs doubles) Phi_k. */
+bl_status bl_gradient(bl_problem* prob, const int32_t* pairs, int32_t npairs, const double* theta,
+                      const void* x_packed, void* grad_packed, double* values);
+
+/* out_k = H_k v_k at the current point (matrix-free Hessian action, eq. (2.6)). */
+bl_status bl_hvp(bl_problem* prob, const int32_t* pairs, int32_t npairs, const void* v_packed,
+                 void* out_packed);
+
+/* Refresh the recycle space of each listed pair (Section 3, outer form eq. (3.3)):
+ * W = [U^(i-1), V^(i-1)] is orthonormalised, projected with the current H (and J for RGSV),
+ * the s selected vectors U~ are QR-normalised so that C = H U, C^T C = I (Section 2.2.2), and
+ * for RGSV the estimate operator Z = W~ V~_H diag(mu) of eq. (4.2) is stored.
+ * A pair without a stored basis keeps an empty recycle space. */
+bl_status bl_ritz_update(bl_problem* prob, const int32_t* pairs, int32_t npairs,
+                         const bl_recycle_opts* opts);
+
+/* Solve H_k w_k = g_k for the listed pairs in one batched recycled-CG run (Section 2.2):
+ *   g_packed: device right-hand sides, or NULL for g_k = x^_k - x*_k (grad of 1/2||x - x*||^2);
+ *   w_packed: device, in = warm start (if opts->warm_start), out = solution;
+ *   nsc_scale: host, npairs doubles used by a relative NSC rule, or NULL;
+ *   info: host, npairs entries, or NULL.
+ * The stored Krylov basis V (if opts->store_basis) replaces the previous one.
+ * Returns BL_ENOCONV if a pair hit maxit, BL_EBREAKDOWN if a pair broke down. */
+bl_status bl_hessian_solve(bl_problem* prob, const int32_t* pairs, int32_t npairs,
+                           const bl_krylov_opts* opts, const void* g_packed, void* w_packed,
+                           const double* nsc_scale, bl_solve_info* info);
+
+/* Hypergradient contributions g_k = J_k w_k = -(D^2_{theta x} Phi_k)^T w_k (eq. (2.7)):
+ *   grads: device, npairs x p doubles (row k for listed pair k), or NULL;
+ *   mean_grad: device, p doubles = (1/npairs) sum_k g_k, or NULL;
+ *   loss: host, if non-NULL receives (1/npairs) sum_k 1/2 ||x^_k - x*_k||^2 (eq. (5.2)). */
+bl_status bl_hypergrad(bl_problem* prob, const int32_t* pairs, int32_t npairs, const void* w_packed,
+                       double* grads, double* mean_grad, double* loss);
+
+/* Current recycle dimension and stored basis size of one pair (host values). */
+int32_t bl_recycle_dim(const bl_problem* prob, int32_t pair);
+int32_t bl_basis_size(const bl_problem* prob, int32_t pair);
+
+/* Checkpoint of one pair's recycle state (U, C, Z, Z^T C and sizes) to a host buffer.
+ * bl_recycle_export: with buf == NULL sets *bytes to the size needed; otherwise writes
+ * at most *bytes (BL_EINVAL if too small) and sets *bytes to the size written.
+ * bl_recycle_import: restores a buffer written by bl_recycle_export for a pair of the same
+ * size and precision (BL_EINVAL on any header mismatch or truncation). */
+bl_status bl_recycle_export(bl_problem* prob, int32_t pair, void* buf, size_t* bytes);
+bl_status bl_recycle_import(bl_problem* prob, int32_t pair, const void* buf, size_t bytes);
+
+/* Number of this library's kernel launches since the problem was created (host counter). */
+int64_t bl_launch_count(const bl_problem* prob);
+
+/* Per-kernel-class timing (CUDA events recorded on the problem's stream around each launch
+ * while enabled) and work counters (pixels x columns processed, counted by the kernels).
+ * bl_profile_enable(prob, 1) clears the counters and starts recording; 0 stops.
+ * bl_profile_read synchronises the stream and returns the totals of one class since enable. */
+typedef enum {
+  BL_KC_HVP = 0,        /* fused Hessian action in the Krylov loop (one vector) */
+  BL_KC_HVP_MULTI = 1,  /* Hessian action on the columns of W~ (recycle refresh) */
+  BL_KC_GRAD = 2,       /* fused gradient and value of Phi (lower solve) */
+  BL_KC_JW = 3,         /* J w contraction (hypergradient and refresh) */
+  BL_KC_KRYLOV = 4,     /* recycled-CG vector updates and scalar kernels */
+  BL_KC_LBFGS = 5,      /* L-BFGS vector updates and scalar kernels */
+  BL_KC_GRAM = 6,       /* tall-skinny Gram matrices */
+  BL_KC_GEMM = 7,       /* tall-skinny basis products */
+  BL_KC_DENSE = 8,      /* small FP64 eigen / Cholesky problems */
+  BL_KC_OTHER = 9,      /* reductions, fields, copies */
+  BL_KC_COUNT = 10
+} bl_kernel_class;
+bl_status bl_profile_enable(bl_problem* prob, int32_t enable);
+bl_status bl_profile_read(bl_problem* prob, int32_t kernel_class, double* total_ms, int64_t* launches,
+                          int64_t* pixels);
+
+const char* bl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BL_H_ */

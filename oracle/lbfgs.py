@@ -2,7 +2,8 @@
 
 Two-loop recursion with initial scaling gamma = s^T y / y^T y of the newest
 pair (gamma = 1 before any pair exists).  Armijo backtracking on Phi with
-c1 = 1e-4 and step halving, first trial step 1.  A pair is stored only when
+c1 = 1e-4 and step halving, first trial step 1; `slack` > 0 adds slack * |Phi(x)|
+to the sufficient-decrease bound (0, the plain rule, is the default).  A pair is stored only when
 s^T y > 1e-12 ||s|| ||y||.  Stops when ||grad Phi|| <= gtol.
 """
 from __future__ import annotations
@@ -10,7 +11,7 @@ from __future__ import annotations
 import numpy as np
 
 
-def lbfgs(fun, grad, x0, gtol, m=10, maxit=10000, c1=1e-4, max_backtrack=60):
+def lbfgs(fun, grad, x0, gtol, m=10, maxit=10000, c1=1e-4, max_backtrack=60, slack=0.0):
     x = x0.copy()
     f = fun(x)
     g = grad(x)
@@ -40,7 +41,7 @@ def lbfgs(fun, grad, x0, gtol, m=10, maxit=10000, c1=1e-4, max_backtrack=60):
             xn = x + t * d
             fn = fun(xn)
             evals += 1
-            if fn <= f + c1 * t * gd:
+            if fn <= f + c1 * t * gd + slack * abs(f):
                 break
             t *= 0.5
         gn = grad(xn)

@@ -1,0 +1,215 @@
+// Internal declarations shared by the translation units of libbl.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bl.h"
+
+namespace bl {
+
+// ---------------------------------------------------------------------------------------------
+// Error handling: a thread-local message, set by fail(); every entry point returns a status.
+void set_error(const std::string& msg);
+std::string error_copy();
+bl_status fail(bl_status st, const std::string& msg);
+
+#define BL_CUDA_TRY(expr)                                                                  \
+  do {                                                                                     \
+    cudaError_t _e = (expr);                                                               \
+    if (_e != cudaSuccess)                                                                 \
+      return ::bl::fail(BL_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(_e));     \
+  } while (0)
+
+#define BL_LAUNCH_CHECK(prob)                                                              \
+  do {                                                                                     \
+    (prob)->launches++;                                                                    \
+    cudaError_t _e = cudaGetLastError();                                                   \
+    if (_e != cudaSuccess)                                                                 \
+      return ::bl::fail(BL_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(_e));\
+  } while (0)
+
+// ---------------------------------------------------------------------------------------------
+// Geometry.  Every batched n-vector is the concatenation of the pairs' images (pair k at
+// pixel offset off_k).  A batched n x M matrix keeps, for pair k, a column-major n_k x M
+// block starting at off_k * M (column j of pair k at off_k * M + j * n_k).
+
+constexpr int kTileRegion = 64;           // side of the step-1 region of the fused stencil
+constexpr int kHalo = 8;                  // staged halo: covers 2 r_b (r_b <= 4) and 2 r_f (r_f <= 3)
+constexpr int kStencilThreads = 256;
+constexpr int kChunk = 4096;              // pixels per block of the elementwise kernels
+constexpr int kChunkThreads = 256;
+constexpr int kMaxFilters = 64;
+constexpr int kMaxTM = 96;                // max columns of W (recycle + basis)
+constexpr int kMaxHistory = 16;           // L-BFGS memory
+
+__host__ __device__ constexpr int tile_out(int F) { return (kTileRegion - 2 * (F / 2)) & ~3; }
+
+struct PairDev {
+  int h, w;
+  long long n, off;
+  int rb;
+  int tbeg, tend;      // tiles [tbeg, tend) of this pair
+  int cbeg, cend;      // chunks [cbeg, cend)
+  float gf[2 * BL_MAX_BLUR_RADIUS + 1];
+  double gd[2 * BL_MAX_BLUR_RADIUS + 1];
+};
+
+struct TileDev { int pair, oy, ox; };
+struct ChunkDev { int pair; long long start; int len; };
+
+// Per-pair scalar state of a Krylov solve (FP64 recurrences).
+struct SolveState {
+  double rho, rho_new, alpha, beta, pq, est, tol, gnorm2;
+  int active, iters, status, maxit;
+};
+
+// Per-pair L-BFGS state.
+struct LbfgsState {
+  double f, f_trial, gtd, t, gnorm, gtol, rho_hist[kMaxHistory], a_hist[kMaxHistory], gamma;
+  int active, accepted, iters, status, hist_count, hist_head, backtracks, pad;
+};
+
+struct ProfEvent {
+  cudaEvent_t a, b;
+  int cls;
+};
+
+struct PairHost {
+  int h, w;
+  long long n, off;
+  int rb;
+  double sigma;
+  int tbeg, tend, cbeg, cend;
+};
+
+}  // namespace bl
+
+struct bl_problem {
+  int K = 0;
+  int prec = BL_FP32;
+  size_t esz = 4;
+  bl_reg_desc reg{};
+  int p = 0, N = 0, F = 1, rf = 0;
+  int SMAX = 0, KMAX = 0, TM = 0;
+  std::vector<bl::PairHost> ph;
+  long long n_tot = 0;
+  cudaStream_t stream = nullptr;
+  int64_t launches = 0;
+  int n_tiles = 0, n_chunks = 0;
+
+  bl::PairDev* d_pairs = nullptr;
+  bl::TileDev* d_tiles = nullptr;
+  bl::ChunkDev* d_chunks = nullptr;
+
+  void *y = nullptr, *xstar = nullptr, *xhat = nullptr;
+  void *fu = nullptr, *fd = nullptr;       // FoE fields u_j = k_j * x^, d_j = e^{alpha_j} phi''(u_j)
+  double* theta = nullptr;                 // p
+  float* taps_f = nullptr;                 // N * F * F
+  double* taps_d = nullptr;
+  double* ealpha = nullptr;                // N: exp(alpha_j)  (TV: [exp(theta_0)])
+  bool point_set = false;
+
+  // Krylov vectors and recycle state
+  void *r = nullptr, *pv = nullptr, *q = nullptr, *w = nullptr, *g = nullptr, *tmp = nullptr;
+  void *U = nullptr, *C = nullptr, *Z = nullptr, *V = nullptr;
+  void *W = nullptr, *Wt = nullptr, *HWt = nullptr;
+  bl::SolveState* st = nullptr;
+  double *c = nullptr, *zc = nullptr, *e = nullptr, *ztr = nullptr, *ztc = nullptr;
+  int* d_s = nullptr;       // recycle dimension per pair
+  int* d_hasz = nullptr;    // pair has an NSC operator Z
+  int* d_active = nullptr;  // generic per-pair mask
+  int* d_cols = nullptr;    // per-pair column counts for multi-column kernels
+  int* d_flag = nullptr;    // any-active flag (device)
+  int* h_flag = nullptr;    // pinned host mirror
+  std::vector<int> s_k, kb_k, hz_k, head_k;
+
+  // dense small-matrix workspace (FP64)
+  double *dG = nullptr, *dT = nullptr, *dJ = nullptr, *dY = nullptr, *dY2 = nullptr, *dY3 = nullptr;
+  int* d_tk = nullptr;      // reduced basis size per pair
+
+  // L-BFGS
+  void *lx = nullptr, *lg = nullptr, *ld = nullptr, *lxt = nullptr, *lgt = nullptr, *lq = nullptr;
+  void *S = nullptr, *Yh = nullptr;
+  bl::LbfgsState* lst = nullptr;
+  int MH = 0;
+
+  // profiling: events per launch and device pixel counters per kernel class
+  bool prof = false;
+  std::vector<bl::ProfEvent> prof_ev;
+  size_t prof_used = 0;
+  double prof_ms[BL_KC_COUNT] = {};
+  int64_t prof_n[BL_KC_COUNT] = {};
+  unsigned long long* d_pix = nullptr;   // BL_KC_COUNT counters
+
+  // partial sums
+  double* tpart = nullptr;
+  size_t tpart_cap = 0;
+  double* cpart = nullptr;
+  size_t cpart_cap = 0;
+  double* vals = nullptr;   // per-pair reduced values (K * 8)
+};
+
+namespace bl {
+
+// Profiling scope: records a CUDA event pair around the launches it encloses when enabled.
+struct ProfScope {
+  bl_problem* P;
+  int slot;
+  ProfScope(bl_problem* p, int cls);
+  ~ProfScope();
+};
+unsigned long long* pix_counter(bl_problem* P, int cls);   // null when profiling is off
+
+// Allocation helper (tracks nothing; caller frees in bl_problem_destroy).
+bl_status dalloc(void** ptr, size_t bytes);
+bl_status ensure_tpart(bl_problem* P, size_t doubles);
+bl_status ensure_cpart(bl_problem* P, size_t doubles);
+bl_status set_active_pairs(bl_problem* P, const int32_t* pairs, int32_t npairs);
+bl_status gather_packed(bl_problem* P, const int32_t* pairs, int32_t npairs, const void* packed,
+                        void* batched);
+bl_status scatter_packed(bl_problem* P, const int32_t* pairs, int32_t npairs, const void* batched,
+                         void* packed);
+bl_status check_pairs(const bl_problem* P, const int32_t* pairs, int32_t npairs);
+
+// ---- stencil.cu ----
+// out = H v for `cols` columns of a batched matrix (mult = 0: plain batched vector).
+// With dots_s != null (FoE only) the tile partials of p^T q, C^T q (dots_s[k] columns) and Z^T q
+// (if dots_hz[k]) are written to tpart, layout [tile][1 + 2 SMAX].
+bl_status launch_hvp(bl_problem* P, const void* in, void* out, int mult, int cols, const int* mask,
+                     const int* dots_s, const int* dots_hz);
+bl_status launch_grad(bl_problem* P, const void* x, void* grad, const int* mask, double* values);
+bl_status launch_fields(bl_problem* P, const int* mask);
+bl_status launch_forward(bl_problem* P, const void* x, void* out, const int* mask);
+// J w for `cols` columns: per-pair results (K x cols x p doubles, [k][col][m]) in out.
+bl_status launch_jw(bl_problem* P, const void* in, int mult, int cols, const int* mask, double* out);
+bl_status load_theta(bl_problem* P, const double* theta);
+
+// ---- krylov.cu ----
+bl_status run_hessian_solve(bl_problem* P, const int* mask_host, const bl_krylov_opts* o,
+                            const void* g_batched, const double* nsc_scale_batched,
+                            std::vector<bl_solve_info>& info);
+
+// ---- recycle.cu ----
+bl_status run_ritz_update(bl_problem* P, const std::vector<int>& mask_host,
+                          const bl_recycle_opts* o);
+
+// ---- lbfgs.cu ----
+bl_status run_lower_solve(bl_problem* P, const std::vector<int>& mask_host, const bl_lbfgs_opts* o,
+                          std::vector<bl_solve_info>& info);
+
+// ---- vec.cu: batched vector helpers ----
+// Sum per-unit partials (units = tiles or chunks; layout part[(col * n_units + u) * ncomp + m])
+// over the units of each pair: out[(k * cols + col) * ncomp + m].
+bl_status reduce_units(bl_problem* P, const double* part, int ncomp, int cols, bool tiles, const int* mask,
+                       const int* colcnt, double* out);
+// Reduce per-chunk partials: out[k * ncomp + c] = sum over chunks of pair k (masked pairs only).
+bl_status reduce_chunk_partials(bl_problem* P, int ncomp, const int* mask, double* out);
+bl_status reduce_tile_partials(bl_problem* P, int ncomp, int cols, const int* mask, double* out);
+// dot products per pair: out[k] = sum_i a_i b_i (FP64 accumulation).
+bl_status batched_dot(bl_problem* P, const void* a, const void* b, const int* mask, double* out);
+
+}  // namespace bl

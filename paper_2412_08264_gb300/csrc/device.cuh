@@ -1,0 +1,82 @@
+// Device-side helpers: penalty functions of eq. (5.1), reductions, per-pair addressing.
+#pragma once
+
+#include "common.cuh"
+
+namespace bl {
+
+// phi and its derivatives (eq. (5.1)); kind = bl_phi_kind.
+template <typename T>
+__device__ __forceinline__ void phi_all(T s, T eps, int kind, T& f, T& d1, T& d2) {
+  if (kind == BL_PHI_CHARBONNIER) {
+    T q = s * s + eps * eps;
+    T inv = rsqrt(q);
+    f = q * inv;
+    d1 = s * inv;
+    d2 = eps * eps * inv * inv * inv;
+  } else if (kind == BL_PHI_SQ) {
+    f = s * s;
+    d1 = T(2) * s;
+    d2 = T(2);
+  } else {
+    T q = T(1) + s * s;
+    T iq = T(1) / q;
+    f = log(q);
+    d1 = T(2) * s * iq;
+    d2 = T(2) * (T(1) - s * s) * iq * iq;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ T phi_d1(T s, T eps, int kind) {
+  if (kind == BL_PHI_CHARBONNIER) return s * rsqrt(s * s + eps * eps);
+  if (kind == BL_PHI_SQ) return T(2) * s;
+  return T(2) * s / (T(1) + s * s);
+}
+
+template <typename T>
+__device__ __forceinline__ T phi_d2(T s, T eps, int kind) {
+  if (kind == BL_PHI_CHARBONNIER) {
+    T inv = rsqrt(s * s + eps * eps);
+    return eps * eps * inv * inv * inv;
+  }
+  if (kind == BL_PHI_SQ) return T(2);
+  T q = T(1) + s * s;
+  return T(2) * (T(1) - s * s) / (q * q);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum one value over the block; result valid in every thread.  red: >= 33 doubles of smem.
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = (threadIdx.x < NT / 32) ? red[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+    if (threadIdx.x == 0) red[32] = t;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// Column j of pair `pr` in a batched n x mult matrix (mult = 0: plain batched vector).
+template <typename T>
+__device__ __forceinline__ T* col_ptr(T* base, const PairDev& pr, int mult, int j) {
+  return mult ? base + pr.off * mult + (long long)j * pr.n : base + pr.off;
+}
+template <typename T>
+__device__ __forceinline__ const T* col_ptr(const T* base, const PairDev& pr, int mult, int j) {
+  return mult ? base + pr.off * mult + (long long)j * pr.n : base + pr.off;
+}
+
+}  // namespace bl

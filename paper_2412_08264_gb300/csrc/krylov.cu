@@ -1,0 +1,553 @@
+// Batched recycled conjugate gradient for H_k w_k = g_k (Section 2.2, stopping rules of Section 4).
+//
+// Augmented CG over the recycle space U_k with C_k = H_k U_k, C_k^T C_k = I:
+//   init   r = g - H w0;  c0 = C^T r;  w += U c0;  r -= C c0;  p = r;  rho = r^T r;  z = 0
+//   loop   q = H p;  c = C^T q;  alpha = rho / p^T q;  w += alpha p;  z -= alpha c;
+//          r -= alpha (q - C c);  beta = rho' / rho;  p = r + beta p
+//   end    w += U z
+// which is CG on P H P (P = I - C C^T) with the recycle-space coefficients gathered in z, so that
+// g - H (w + U z) = r and C^T r = 0 hold throughout (the augmentation of Algorithm 3 carried
+// over to CG).  The hypergradient-error estimate of eq. (4.2), ||Z^T r||, is carried by the
+// recurrence Z^T r' = Z^T r - alpha (Z^T q - (Z^T C) c).
+//
+// All pairs advance together: vectors are batched over pairs, every per-pair scalar (rho, alpha,
+// beta, the s-vectors c, z, Z^T r) lives on the device in FP64, and each kernel skips the pairs
+// whose `active` flag is cleared (converged, iteration cap or breakdown).  The Hessian action
+// of the FoE regulariser computes p^T q, C^T q and Z^T q in its epilogue.
+#include <cmath>
+
+#include "common.cuh"
+#include "device.cuh"
+
+namespace bl {
+
+struct KrylovArgs {
+  const PairDev* pairs;
+  const ChunkDev* chunks;
+  SolveState* st;
+  const int* s_k;     // effective recycle dimension (0 for plain CG)
+  const int* hasz;    // NSC operator present and used
+  int SMAX, KMAX;
+  double* c;          // K x SMAX
+  double* zc;         // K x SMAX
+  double* e;          // K x SMAX
+  double* ztr;        // K x SMAX
+  const double* ztc;  // K x SMAX x SMAX, row i = Z_i^T C
+  double* cpart;
+  const double* tpart;
+  int n_tiles, n_chunks;
+};
+
+// r = g - q (warm) or r = g, w = 0 (cold); partials [0] ||g||^2, [1..s] C^T r.
+template <typename T>
+__global__ void k_init_r(KrylovArgs a, const T* g, const T* q, T* r, T* w, const T* C, int warm,
+                         const int* mask) {
+  __shared__ double red[8 * 65];
+  const ChunkDev ch = a.chunks[blockIdx.x];
+  if (!mask[ch.pair]) return;
+  const PairDev pr = a.pairs[ch.pair];
+  const int s = a.s_k[ch.pair];
+  const int ncomp = 1 + a.SMAX;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const T* Cb = C + pr.off * a.SMAX;
+  for (int cc = 0; cc <= s; cc += 64) {
+    // pass over up to 64 components at a time; component 0 also writes r (and w)
+    const int cnt = min(64, s + 1 - cc);
+    for (int m = 0; m < cnt; ++m) {
+      const int comp = cc + m;
+      double sum = 0.0;
+      for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
+        const long long li = ch.start + t, gi = pr.off + li;
+        T rv;
+        if (comp == 0) {
+          const T gv = g[gi];
+          rv = warm ? gv - q[gi] : gv;
+          r[gi] = rv;
+          if (!warm) w[gi] = T(0);
+          sum += (double)gv * (double)gv;
+        } else {
+          rv = r[gi];
+          sum += (double)Cb[(long long)(comp - 1) * pr.n + li] * (double)rv;
+        }
+      }
+      sum = warp_sum(sum);
+      if (lane == 0) red[wid * 65 + m] = sum;
+      if (comp == 0) __syncthreads();   // r must be written before the C^T r components read it
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < cnt) {
+      double t = 0.0;
+      for (int q2 = 0; q2 < kChunkThreads / 32; ++q2) t += red[q2 * 65 + threadIdx.x];
+      a.cpart[(size_t)blockIdx.x * ncomp + cc + threadIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// c0 = C^T r, ||g||^2 per pair
+__global__ void k_scalar_init1(KrylovArgs a, const int* mask) {
+  const int k = blockIdx.x;
+  if (!mask[k]) return;
+  const PairDev pr = a.pairs[k];
+  const int s = a.s_k[k];
+  const int ncomp = 1 + a.SMAX;
+  for (int m = threadIdx.x; m <= s; m += blockDim.x) {
+    double t = 0.0;
+    for (int u = pr.cbeg; u < pr.cend; ++u) t += a.cpart[(size_t)u * ncomp + m];
+    if (m == 0) a.st[k].gnorm2 = t;
+    else a.c[k * a.SMAX + m - 1] = t;
+  }
+}
+
+// w += U c0; r -= C c0; p = r; partials [0] rho, [1..nz] Z^T r
+template <typename T>
+__global__ void k_init2(KrylovArgs a, T* w, T* r, T* p, const T* U, const T* C, const T* Z, const int* mask) {
+  __shared__ double red[8 * 65];
+  __shared__ double cs[64];
+  const ChunkDev ch = a.chunks[blockIdx.x];
+  if (!mask[ch.pair]) return;
+  const PairDev pr = a.pairs[ch.pair];
+  const int s = a.s_k[ch.pair];
+  const int nz = a.hasz[ch.pair] ? s : 0;
+  const int ncomp = 1 + a.SMAX;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if ((int)threadIdx.x < s) cs[threadIdx.x] = a.c[ch.pair * a.SMAX + threadIdx.x];
+  __syncthreads();
+  const T* Ub = U + pr.off * a.SMAX;
+  const T* Cb = C + pr.off * a.SMAX;
+  const T* Zb = Z + pr.off * a.SMAX;
+  double rho = 0.0;
+  for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
+    const long long li = ch.start + t, gi = pr.off + li;
+    double uc = 0.0, ccv = 0.0;
+    for (int j = 0; j < s; ++j) {
+      uc += cs[j] * (double)Ub[(long long)j * pr.n + li];
+      ccv += cs[j] * (double)Cb[(long long)j * pr.n + li];
+    }
+    const T wn = w[gi] + (T)uc;
+    const T rn = r[gi] - (T)ccv;
+    w[gi] = wn;
+    r[gi] = rn;
+    p[gi] = rn;
+    rho += (double)rn * (double)rn;
+  }
+  rho = warp_sum(rho);
+  if (lane == 0) red[wid * 65] = rho;
+  __syncthreads();
+  for (int m = 0; m < nz; ++m) {
+    double sum = 0.0;
+    for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
+      const long long li = ch.start + t;
+      sum += (double)Zb[(long long)m * pr.n + li] * (double)r[pr.off + li];
+    }
+    sum = warp_sum(sum);
+    if (lane == 0) red[wid * 65 + 1 + (m & 63)] = sum;
+    if ((m & 63) == 63 || m == nz - 1) {
+      __syncthreads();
+      const int base = (m & ~63);
+      const int cnt = m - base + 1;
+      if ((int)threadIdx.x < cnt) {
+        double tt = 0.0;
+        for (int q2 = 0; q2 < kChunkThreads / 32; ++q2) tt += red[q2 * 65 + 1 + threadIdx.x];
+        a.cpart[(size_t)blockIdx.x * ncomp + 1 + base + threadIdx.x] = tt;
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) {
+    double tt = 0.0;
+    for (int q2 = 0; q2 < kChunkThreads / 32; ++q2) tt += red[q2 * 65];
+    a.cpart[(size_t)blockIdx.x * ncomp] = tt;
+  }
+}
+
+// rho, Z^T r, tolerance and the active flags
+__global__ void k_scalar_init2(KrylovArgs a, const int* mask, int stop_nsc, double tol, int relative,
+                               const double* nsc_scale, int maxit, int* flag) {
+  __shared__ double sh[65];
+  const int k = blockIdx.x;
+  if (!mask[k]) return;
+  const PairDev pr = a.pairs[k];
+  const int s = a.s_k[k];
+  const int nz = a.hasz[k] ? s : 0;
+  const int ncomp = 1 + a.SMAX;
+  for (int m = threadIdx.x; m <= nz; m += blockDim.x) {
+    double t = 0.0;
+    for (int u = pr.cbeg; u < pr.cend; ++u) t += a.cpart[(size_t)u * ncomp + m];
+    if (m == 0) sh[64] = t;
+    else a.ztr[k * a.SMAX + m - 1] = t;
+  }
+  for (int m = threadIdx.x; m < a.SMAX; m += blockDim.x) a.zc[k * a.SMAX + m] = 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    SolveState S = a.st[k];
+    S.rho = sh[64];
+    S.iters = 0;
+    S.status = BL_OK;
+    S.maxit = maxit;
+    const bool nsc = stop_nsc && nz > 0;
+    double est, scale;
+    if (nsc) {
+      double z2 = 0.0;
+      for (int m = 0; m < nz; ++m) z2 += a.ztr[k * a.SMAX + m] * a.ztr[k * a.SMAX + m];
+      est = sqrt(z2);
+      scale = (relative && nsc_scale) ? nsc_scale[k] : 1.0;
+    } else {
+      est = sqrt(S.rho);
+      scale = (relative || stop_nsc) ? sqrt(S.gnorm2) : 1.0;
+    }
+    S.tol = tol * scale;
+    S.est = est;
+    S.active = (est >= S.tol && maxit > 0 && S.rho > 0.0) ? 1 : 0;
+    if (!isfinite(S.rho)) {
+      S.active = 0;
+      S.status = BL_EBREAKDOWN;
+    }
+    a.st[k] = S;
+    if (S.active) atomicAdd(flag, 1);
+  }
+}
+
+// generic chunk dots for problems without the fused epilogue: [0] p^T q, [1..s] C^T q, [1+SMAX..] Z^T q
+template <typename T>
+__global__ void k_dots(KrylovArgs a, const T* p, const T* q, const T* C, const T* Z) {
+  __shared__ double red[8 * 65];
+  const ChunkDev ch = a.chunks[blockIdx.x];
+  if (!a.st[ch.pair].active) return;
+  const PairDev pr = a.pairs[ch.pair];
+  const int s = a.s_k[ch.pair];
+  const int nz = a.hasz[ch.pair] ? s : 0;
+  const int ncomp = 1 + 2 * a.SMAX;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const T* Cb = C + pr.off * a.SMAX;
+  const T* Zb = Z + pr.off * a.SMAX;
+  const int total = 1 + s + nz;
+  for (int base = 0; base < total; base += 64) {
+    const int cnt = min(64, total - base);
+    for (int m = 0; m < cnt; ++m) {
+      const int comp = base + m;
+      const T* src = comp == 0 ? p + pr.off
+                               : (comp <= s ? Cb + (long long)(comp - 1) * pr.n : Zb + (long long)(comp - 1 - s) * pr.n);
+      double sum = 0.0;
+      for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
+        const long long li = ch.start + t;
+        sum += (double)src[li] * (double)q[pr.off + li];
+      }
+      sum = warp_sum(sum);
+      if (lane == 0) red[wid * 65 + m] = sum;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < cnt) {
+      double tt = 0.0;
+      for (int q2 = 0; q2 < kChunkThreads / 32; ++q2) tt += red[q2 * 65 + threadIdx.x];
+      const int comp = base + threadIdx.x;
+      const int slot = comp <= s ? comp : comp - s + a.SMAX;
+      a.cpart[(size_t)blockIdx.x * ncomp + slot] = tt;
+    }
+    __syncthreads();
+  }
+}
+
+// alpha, c = C^T q, z -= alpha c, Z^T r -= alpha (Z^T q - Z^T C c); breakdown check
+__global__ void k_scalar1(KrylovArgs a, int use_tiles) {
+  __shared__ double sh[2 * 64 + 1];
+  __shared__ double alpha_s;
+  const int k = blockIdx.x;
+  if (!a.st[k].active) return;
+  const PairDev pr = a.pairs[k];
+  const int s = a.s_k[k];
+  const int nz = a.hasz[k] ? s : 0;
+  const int ncomp = 1 + 2 * a.SMAX;
+  const double* part = use_tiles ? a.tpart : a.cpart;
+  const int beg = use_tiles ? pr.tbeg : pr.cbeg, end = use_tiles ? pr.tend : pr.cend;
+  for (int m = threadIdx.x; m < 1 + s + nz; m += blockDim.x) {
+    const int slot = m <= s ? m : m - s + a.SMAX;
+    double t = 0.0;
+    for (int u = beg; u < end; ++u) t += part[(size_t)u * ncomp + slot];
+    sh[m] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    SolveState S = a.st[k];
+    S.pq = sh[0];
+    if (!(S.pq > 0.0) || !isfinite(S.pq)) {
+      S.active = 0;
+      S.status = BL_EBREAKDOWN;
+      alpha_s = 0.0;
+    } else {
+      S.alpha = S.rho / S.pq;
+      alpha_s = S.alpha;
+    }
+    a.st[k] = S;
+  }
+  __syncthreads();
+  const double al = alpha_s;
+  for (int m = threadIdx.x; m < s; m += blockDim.x) {
+    a.c[k * a.SMAX + m] = sh[1 + m];
+    a.zc[k * a.SMAX + m] -= al * sh[1 + m];
+  }
+  for (int m = threadIdx.x; m < nz; m += blockDim.x) {
+    double ztcc = 0.0;
+    for (int j = 0; j < s; ++j) ztcc += a.ztc[((size_t)k * a.SMAX + m) * a.SMAX + j] * sh[1 + j];
+    a.e[k * a.SMAX + m] = sh[1 + s + m];
+    a.ztr[k * a.SMAX + m] -= al * (sh[1 + s + m] - ztcc);
+  }
+}
+
+// w += alpha p; V[:, it] = r / ||r||; r -= alpha (q - C c); partial rho' = r^T r
+template <typename T>
+__global__ void k_update(KrylovArgs a, T* w, T* r, const T* p, const T* q, const T* C, T* V, int store) {
+  __shared__ double red[40];
+  __shared__ double cs[64];
+  const ChunkDev ch = a.chunks[blockIdx.x];
+  const SolveState S = a.st[ch.pair];
+  if (!S.active) return;
+  const PairDev pr = a.pairs[ch.pair];
+  const int s = a.s_k[ch.pair];
+  if ((int)threadIdx.x < s) cs[threadIdx.x] = a.c[ch.pair * a.SMAX + threadIdx.x];
+  __syncthreads();
+  const T* Cb = C + pr.off * a.SMAX;
+  T* Vc = store ? V + pr.off * a.KMAX + (long long)(S.iters % a.KMAX) * pr.n : nullptr;
+  const double inv_nr = 1.0 / sqrt(S.rho);
+  const T al = (T)S.alpha;
+  double rho = 0.0;
+  for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
+    const long long li = ch.start + t, gi = pr.off + li;
+    const T ro = r[gi];
+    if (store) Vc[li] = (T)((double)ro * inv_nr);
+    w[gi] = fma(al, p[gi], w[gi]);
+    double ccv = 0.0;
+    for (int j = 0; j < s; ++j) ccv += cs[j] * (double)Cb[(long long)j * pr.n + li];
+    const T rn = ro - al * (q[gi] - (T)ccv);
+    r[gi] = rn;
+    rho += (double)rn * (double)rn;
+  }
+  rho = block_sum<kChunkThreads>(rho, red);
+  if (threadIdx.x == 0) a.cpart[blockIdx.x] = rho;
+}
+
+// rho', beta, stopping test
+__global__ void k_scalar2(KrylovArgs a, int stop_nsc, int* flag) {
+  __shared__ double sh;
+  const int k = blockIdx.x;
+  if (!a.st[k].active) return;
+  const PairDev pr = a.pairs[k];
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int u = pr.cbeg; u < pr.cend; ++u) t += a.cpart[u];
+    sh = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    SolveState S = a.st[k];
+    const int s = a.s_k[k];
+    const int nz = a.hasz[k] ? s : 0;
+    S.rho_new = sh;
+    S.beta = sh / S.rho;
+    S.rho = sh;
+    S.iters += 1;
+    if (stop_nsc && nz > 0) {
+      double z2 = 0.0;
+      for (int m = 0; m < nz; ++m) z2 += a.ztr[k * a.SMAX + m] * a.ztr[k * a.SMAX + m];
+      S.est = sqrt(z2);
+    } else {
+      S.est = sqrt(sh);
+    }
+    if (!isfinite(sh)) {
+      S.active = 0;
+      S.status = BL_EBREAKDOWN;
+    } else if (S.est < S.tol || sh == 0.0) {
+      S.active = 0;
+    } else if (S.iters >= S.maxit) {
+      S.active = 0;
+      S.status = BL_ENOCONV;
+    }
+    a.st[k] = S;
+    if (S.active) atomicAdd(flag, 1);
+  }
+}
+
+template <typename T>
+__global__ void k_pupdate(KrylovArgs a, const T* r, T* p) {
+  const ChunkDev ch = a.chunks[blockIdx.x];
+  const SolveState S = a.st[ch.pair];
+  if (!S.active) return;
+  const PairDev pr = a.pairs[ch.pair];
+  const T be = (T)S.beta;
+  for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
+    const long long gi = pr.off + ch.start + t;
+    p[gi] = fma(be, p[gi], r[gi]);
+  }
+}
+
+// w += U z
+template <typename T>
+__global__ void k_finalize(KrylovArgs a, T* w, const T* U, const int* mask) {
+  __shared__ double zs[64];
+  const ChunkDev ch = a.chunks[blockIdx.x];
+  if (!mask[ch.pair]) return;
+  const PairDev pr = a.pairs[ch.pair];
+  const int s = a.s_k[ch.pair];
+  if (s == 0) return;
+  if ((int)threadIdx.x < s) zs[threadIdx.x] = a.zc[ch.pair * a.SMAX + threadIdx.x];
+  __syncthreads();
+  const T* Ub = U + pr.off * a.SMAX;
+  for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
+    const long long li = ch.start + t, gi = pr.off + li;
+    double uz = 0.0;
+    for (int j = 0; j < s; ++j) uz += zs[j] * (double)Ub[(long long)j * pr.n + li];
+    w[gi] = w[gi] + (T)uz;
+  }
+}
+
+__global__ void k_copy_active(const SolveState* st, int* out, int K) {
+  for (int k = threadIdx.x; k < K; k += blockDim.x) out[k] = st[k].active;
+}
+
+template <typename T>
+static bl_status solve_impl(bl_problem* P, const int* mask_host, const bl_krylov_opts* o, const void* g,
+                            const double* nsc_scale, std::vector<bl_solve_info>& info) {
+  const int K = P->K;
+  // effective recycle dims and NSC flags for this solve
+  std::vector<int> s_eff(K, 0), hz_eff(K, 0);
+  for (int k = 0; k < K; ++k) {
+    if (!mask_host[k]) continue;
+    s_eff[k] = (o->method == BL_SOLVE_RCG) ? P->s_k[k] : 0;
+    hz_eff[k] = (o->method == BL_SOLVE_RCG && o->stop == BL_STOP_NSC && P->hz_k[k]) ? 1 : 0;
+  }
+  int* d_seff = P->d_cols;          // reuse: per-pair ints
+  int* d_hz = P->d_cols + K;
+  BL_CUDA_TRY(cudaMemcpyAsync(d_seff, s_eff.data(), K * sizeof(int), cudaMemcpyHostToDevice, P->stream));
+  BL_CUDA_TRY(cudaMemcpyAsync(d_hz, hz_eff.data(), K * sizeof(int), cudaMemcpyHostToDevice, P->stream));
+  double* d_scale = P->vals;        // K doubles
+  if (nsc_scale)
+    BL_CUDA_TRY(cudaMemcpyAsync(d_scale, nsc_scale, K * sizeof(double), cudaMemcpyHostToDevice, P->stream));
+
+  bl_status st = ensure_cpart(P, (size_t)P->n_chunks * (1 + 2 * P->SMAX));
+  if (st != BL_OK) return st;
+  const bool fused = P->reg.kind == BL_REG_FOE;
+  if (fused) {
+    st = ensure_tpart(P, (size_t)P->n_tiles * (1 + 2 * P->SMAX));
+    if (st != BL_OK) return st;
+  }
+  KrylovArgs a{};
+  a.pairs = P->d_pairs;
+  a.chunks = P->d_chunks;
+  a.st = P->st;
+  a.s_k = d_seff;
+  a.hasz = d_hz;
+  a.SMAX = P->SMAX;
+  a.KMAX = P->KMAX;
+  a.c = P->c;
+  a.zc = P->zc;
+  a.e = P->e;
+  a.ztr = P->ztr;
+  a.ztc = P->ztc;
+  a.cpart = P->cpart;
+  a.tpart = P->tpart;
+  a.n_tiles = P->n_tiles;
+  a.n_chunks = P->n_chunks;
+  const int* mask = P->d_active;
+  T* w = (T*)P->w;
+  T* r = (T*)P->r;
+  T* p = (T*)P->pv;
+  T* q = (T*)P->q;
+  const T* U = (const T*)P->U;
+  const T* C = (const T*)P->C;
+  const T* Z = (const T*)P->Z;
+  const bool warm = o->warm_start != 0;
+
+  // ---- init ----
+  if (warm) {
+    st = launch_hvp(P, w, q, 0, 0, mask, nullptr, nullptr);
+    if (st != BL_OK) return st;
+  }
+  {
+  ProfScope ps(P, BL_KC_KRYLOV);
+  k_init_r<T><<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a, (const T*)g, q, r, w, C, warm ? 1 : 0, mask);
+  BL_LAUNCH_CHECK(P);
+  k_scalar_init1<<<K, 128, 0, P->stream>>>(a, mask);
+  BL_LAUNCH_CHECK(P);
+  k_init2<T><<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a, w, r, p, U, C, Z, mask);
+  BL_LAUNCH_CHECK(P);
+  BL_CUDA_TRY(cudaMemsetAsync(P->d_flag, 0, sizeof(int), P->stream));
+  k_scalar_init2<<<K, 128, 0, P->stream>>>(a, mask, o->stop == BL_STOP_NSC ? 1 : 0, o->tol, o->relative,
+                                           nsc_scale ? d_scale : nullptr, o->maxit, P->d_flag);
+  BL_LAUNCH_CHECK(P);
+  }
+  BL_CUDA_TRY(cudaMemcpyAsync(P->h_flag, P->d_flag, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+  BL_CUDA_TRY(cudaStreamSynchronize(P->stream));
+
+  // ---- iterations ----
+  // the per-pair `active` flags gate every kernel; the host only polls the any-active count
+  int* d_itmask = P->d_active + K; // per-pair active copy for the stencil mask
+  for (int it = 0; it < o->maxit && *P->h_flag > 0; ++it) {
+    // stencil mask = active flags of this iteration
+    {
+      ProfScope ps(P, BL_KC_KRYLOV);
+      k_copy_active<<<1, 128, 0, P->stream>>>(P->st, d_itmask, K);
+      BL_LAUNCH_CHECK(P);
+    }
+    st = launch_hvp(P, p, q, 0, 0, d_itmask, fused ? d_seff : nullptr, fused ? d_hz : nullptr);
+    if (st != BL_OK) return st;
+    ProfScope ps(P, BL_KC_KRYLOV);
+    if (!fused) {
+      k_dots<T><<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a, p, q, C, Z);
+      BL_LAUNCH_CHECK(P);
+    }
+    k_scalar1<<<K, 128, 0, P->stream>>>(a, fused ? 1 : 0);
+    BL_LAUNCH_CHECK(P);
+    k_update<T><<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a, w, r, p, q, C, (T*)P->V,
+                                                               (o->store_basis && P->KMAX > 0) ? 1 : 0);
+    BL_LAUNCH_CHECK(P);
+    BL_CUDA_TRY(cudaMemsetAsync(P->d_flag, 0, sizeof(int), P->stream));
+    k_scalar2<<<K, 32, 0, P->stream>>>(a, o->stop == BL_STOP_NSC ? 1 : 0, P->d_flag);
+    BL_LAUNCH_CHECK(P);
+    k_pupdate<T><<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a, r, p);
+    BL_LAUNCH_CHECK(P);
+    ps.~ProfScope();
+    ps.slot = -1;
+    BL_CUDA_TRY(cudaMemcpyAsync(P->h_flag, P->d_flag, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+    BL_CUDA_TRY(cudaStreamSynchronize(P->stream));
+  }
+  {
+    ProfScope ps(P, BL_KC_KRYLOV);
+    k_finalize<T><<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a, w, U, mask);
+    BL_LAUNCH_CHECK(P);
+  }
+
+  // ---- results ----
+  std::vector<SolveState> hs(K);
+  BL_CUDA_TRY(cudaMemcpyAsync(hs.data(), P->st, K * sizeof(SolveState), cudaMemcpyDeviceToHost, P->stream));
+  std::vector<double> hztr((size_t)K * P->SMAX);
+  if (P->SMAX)
+    BL_CUDA_TRY(cudaMemcpyAsync(hztr.data(), P->ztr, hztr.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                P->stream));
+  BL_CUDA_TRY(cudaStreamSynchronize(P->stream));
+  info.assign(K, bl_solve_info{});
+  for (int k = 0; k < K; ++k) {
+    if (!mask_host[k]) continue;
+    const SolveState& S = hs[k];
+    info[k].iters = S.iters;
+    info[k].status = S.status;
+    info[k].resid = std::sqrt(std::max(S.rho, 0.0));
+    double z2 = 0.0;
+    if (hz_eff[k])
+      for (int m = 0; m < s_eff[k]; ++m) z2 += hztr[(size_t)k * P->SMAX + m] * hztr[(size_t)k * P->SMAX + m];
+    info[k].nsc_est = std::sqrt(z2);
+    info[k].rhs_norm = std::sqrt(std::max(S.gnorm2, 0.0));
+    if (o->store_basis && P->KMAX > 0) {
+      P->kb_k[k] = std::min(S.iters, P->KMAX);
+      P->head_k[k] = S.iters;
+    }
+  }
+  return BL_OK;
+}
+
+bl_status run_hessian_solve(bl_problem* P, const int* mask_host, const bl_krylov_opts* o, const void* g,
+                            const double* nsc_scale, std::vector<bl_solve_info>& info) {
+  return P->prec == BL_FP32 ? solve_impl<float>(P, mask_host, o, g, nsc_scale, info)
+                            : solve_impl<double>(P, mask_host, o, g, nsc_scale, info);
+}
+
+}  // namespace bl

@@ -1,0 +1,394 @@
+// Batched lower-level solve: L-BFGS with Armijo backtracking (Section 5.1), all pairs together.
+//
+// Per iteration and pair: the two-loop recursion over the m most recent (s, y) pairs with
+// initial scaling gamma = s^T y / y^T y of the newest pair (1 before any pair exists), a
+// descent check (restart from -grad if g^T d >= 0), Armijo backtracking with c1 = 1e-4 from
+// step 1 halving the step (an optional slack eps |Phi| on the sufficient-decrease test lets FP32
+// runs accept steps whose change is below FP32 resolution of Phi), and the pair update only
+// when s^T y > 1e-12 ||s|| ||y||.
+// Vectors are FP32 or FP64 by problem precision; every scalar is FP64 on the device.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "device.cuh"
+
+namespace bl {
+
+struct LbArgs {
+  const PairDev* pairs;
+  const ChunkDev* chunks;
+  LbfgsState* st;
+  int MH;
+  double* cpart;    // per chunk, 4 components
+  double* bcoef;    // K x MH: a_i - b_i of the second loop
+};
+
+__device__ __forceinline__ int lb_slot(const LbfgsState& S, int i, int MH) {
+  return (S.hist_head - 1 - i + 2 * MH) % MH;
+}
+
+// X op= ... : mode 0: X = src (copy); 1: X -= a_i Y_i; 2: X = gamma * X; 3: X += (a_i - b_i) S_i;
+// 4: X = -X.  Then partial dot D^T X with D = dotm[:, slot(idot)] (idot >= 0) or D = dotv.
+template <typename T>
+__global__ void k_lb_step(LbArgs a, T* X, const T* src, int mode, const T* axm, int iax, const T* dotm, int idot,
+                          const T* dotv) {
+  __shared__ double red[40];
+  const ChunkDev ch = a.chunks[blockIdx.x];
+  const LbfgsState S = a.st[ch.pair];
+  if (!S.active) return;
+  const PairDev pr = a.pairs[ch.pair];
+  T coef = 0;
+  const T* axc = nullptr;
+  if (mode == 1 && iax < S.hist_count) {
+    coef = (T)(-S.a_hist[iax]);
+    axc = axm + pr.off * a.MH + (long long)lb_slot(S, iax, a.MH) * pr.n;
+  } else if (mode == 3 && iax < S.hist_count) {
+    coef = (T)a.bcoef[ch.pair * a.MH + iax];
+    axc = axm + pr.off * a.MH + (long long)lb_slot(S, iax, a.MH) * pr.n;
+  }
+  const T* dc = nullptr;
+  if (idot >= 0 && idot < S.hist_count) dc = dotm + pr.off * a.MH + (long long)lb_slot(S, idot, a.MH) * pr.n;
+  else if (idot == -2) dc = dotv + pr.off;
+  const T gam = (T)S.gamma;
+  double acc = 0.0;
+  for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
+    const long long li = ch.start + t, gi = pr.off + li;
+    T x;
+    if (mode == 0) x = src[gi];
+    else if (mode == 2) x = gam * X[gi];
+    else if (mode == 4) x = -X[gi];
+    else {
+      x = X[gi];
+      if (axc) x = fma(coef, axc[li], x);
+    }
+    X[gi] = x;
+    if (dc) acc += (double)dc[idot == -2 ? gi - pr.off : li] * (double)x;
+  }
+  acc = block_sum<kChunkThreads>(acc, red);
+  if (threadIdx.x == 0) a.cpart[blockIdx.x] = acc;
+}
+
+// kind 0: a_i = rho_i * sum;  kind 1: b_i = rho_i * sum, bcoef_i = a_i - b_i;
+// kind 2: g^T d = sum (descent check: restart flag if >= 0)
+__global__ void k_lb_coef(LbArgs a, int kind, int i) {
+  const int k = blockIdx.x;
+  LbfgsState& S = a.st[k];
+  if (!S.active || threadIdx.x != 0) return;
+  const PairDev pr = a.pairs[k];
+  double sum = 0.0;
+  for (int u = pr.cbeg; u < pr.cend; ++u) sum += a.cpart[u];
+  if (kind == 0) {
+    S.a_hist[i] = (i < S.hist_count) ? S.rho_hist[lb_slot(S, i, a.MH)] * sum : 0.0;
+  } else if (kind == 1) {
+    const double b = (i < S.hist_count) ? S.rho_hist[lb_slot(S, i, a.MH)] * sum : 0.0;
+    a.bcoef[k * a.MH + i] = (i < S.hist_count) ? S.a_hist[i] - b : 0.0;
+  } else {
+    S.gtd = sum;
+    S.accepted = (sum >= 0.0) ? -1 : 0;   // -1: not a descent direction
+  }
+}
+
+// d = -g for pairs flagged by the descent check; history cleared
+template <typename T>
+__global__ void k_lb_restart(LbArgs a, T* d, const T* g) {
+  __shared__ double red[40];
+  const ChunkDev ch = a.chunks[blockIdx.x];
+  const LbfgsState S = a.st[ch.pair];
+  if (!S.active || S.accepted != -1) return;
+  const PairDev pr = a.pairs[ch.pair];
+  double acc = 0.0;
+  for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
+    const long long gi = pr.off + ch.start + t;
+    d[gi] = -g[gi];
+    acc -= (double)g[gi] * (double)g[gi];
+  }
+  acc = block_sum<kChunkThreads>(acc, red);
+  if (threadIdx.x == 0) a.cpart[blockIdx.x] = acc;
+}
+
+__global__ void k_lb_restart_fix(LbArgs a) {
+  const int k = blockIdx.x;
+  LbfgsState& S = a.st[k];
+  if (!S.active || threadIdx.x != 0 || S.accepted != -1) return;
+  const PairDev pr = a.pairs[k];
+  double sum = 0.0;
+  for (int u = pr.cbeg; u < pr.cend; ++u) sum += a.cpart[u];
+  S.gtd = sum;
+  S.hist_count = 0;
+  S.accepted = 0;
+}
+
+__global__ void k_lb_begin_search(LbArgs a, int* search_mask) {
+  const int k = blockIdx.x;
+  LbfgsState& S = a.st[k];
+  if (threadIdx.x != 0) return;
+  if (S.active) {
+    S.t = 1.0;
+    S.backtracks = 0;
+    S.accepted = 0;
+  }
+  search_mask[k] = S.active;
+}
+
+// x_t = x + t d for searching pairs
+template <typename T>
+__global__ void k_lb_trial(LbArgs a, const int* search_mask, T* xt, const T* x, const T* d) {
+  const ChunkDev ch = a.chunks[blockIdx.x];
+  if (!search_mask[ch.pair]) return;
+  const PairDev pr = a.pairs[ch.pair];
+  const T t = (T)a.st[ch.pair].t;
+  for (int i = threadIdx.x; i < ch.len; i += blockDim.x) {
+    const long long gi = pr.off + ch.start + i;
+    xt[gi] = fma(t, d[gi], x[gi]);
+  }
+}
+
+// Armijo test on the trial values (with the relative slack of the options); halve the step of
+// the pairs that fail
+__global__ void k_lb_armijo(LbArgs a, int* search_mask, const double* vals, double l2, int max_bt, double slack,
+                            int* flag) {
+  const int k = blockIdx.x;
+  if (threadIdx.x != 0 || !search_mask[k]) return;
+  LbfgsState& S = a.st[k];
+  const double ft = vals[k * 3 + 0] + vals[k * 3 + 1] + 0.5 * l2 * vals[k * 3 + 2];
+  if (ft <= S.f + 1e-4 * S.t * S.gtd + slack * fabs(S.f) || S.backtracks + 1 >= max_bt) {
+    S.f_trial = ft;
+    S.accepted = 1;
+    search_mask[k] = 0;
+  } else {
+    S.t *= 0.5;
+    S.backtracks += 1;
+    atomicAdd(flag, 1);
+  }
+}
+
+// store s = x_t - x, y = g_t - g in the head slot, x = x_t, g = g_t; partials s^T y, y^T y, s^T s, g^T g
+template <typename T>
+__global__ void k_lb_accept(LbArgs a, T* x, T* g, const T* xt, const T* gt, T* Sm, T* Ym) {
+  __shared__ double red[40];
+  const ChunkDev ch = a.chunks[blockIdx.x];
+  const LbfgsState S = a.st[ch.pair];
+  if (!S.active) return;
+  const PairDev pr = a.pairs[ch.pair];
+  T* sc = Sm + pr.off * a.MH + (long long)S.hist_head * pr.n;
+  T* yc = Ym + pr.off * a.MH + (long long)S.hist_head * pr.n;
+  double sy = 0, yy = 0, ss = 0, gg = 0;
+  for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
+    const long long li = ch.start + t, gi = pr.off + li;
+    const T xn = xt[gi], gn = gt[gi];
+    const T sv = xn - x[gi], yv = gn - g[gi];
+    sc[li] = sv;
+    yc[li] = yv;
+    x[gi] = xn;
+    g[gi] = gn;
+    sy += (double)sv * (double)yv;
+    yy += (double)yv * (double)yv;
+    ss += (double)sv * (double)sv;
+    gg += (double)gn * (double)gn;
+  }
+  sy = block_sum<kChunkThreads>(sy, red);
+  yy = block_sum<kChunkThreads>(yy, red);
+  ss = block_sum<kChunkThreads>(ss, red);
+  gg = block_sum<kChunkThreads>(gg, red);
+  if (threadIdx.x == 0) {
+    a.cpart[(size_t)blockIdx.x * 4 + 0] = sy;
+    a.cpart[(size_t)blockIdx.x * 4 + 1] = yy;
+    a.cpart[(size_t)blockIdx.x * 4 + 2] = ss;
+    a.cpart[(size_t)blockIdx.x * 4 + 3] = gg;
+  }
+}
+
+__global__ void k_lb_post(LbArgs a, int maxit, int* flag) {
+  const int k = blockIdx.x;
+  LbfgsState& S = a.st[k];
+  if (!S.active || threadIdx.x != 0) return;
+  const PairDev pr = a.pairs[k];
+  double v[4] = {0, 0, 0, 0};
+  for (int u = pr.cbeg; u < pr.cend; ++u)
+    for (int c = 0; c < 4; ++c) v[c] += a.cpart[(size_t)u * 4 + c];
+  const double sy = v[0], yy = v[1], ss = v[2], gg = v[3];
+  if (sy > 1e-12 * sqrt(ss) * sqrt(yy)) {
+    S.rho_hist[S.hist_head] = 1.0 / sy;
+    S.gamma = sy / yy;
+    S.hist_head = (S.hist_head + 1) % a.MH;
+    S.hist_count = min(S.hist_count + 1, a.MH);
+  }
+  if (S.hist_count == 0) S.gamma = 1.0;
+  S.f = S.f_trial;
+  S.gnorm = sqrt(gg);
+  S.iters += 1;
+  if (!isfinite(S.f) || !isfinite(S.gnorm)) {
+    S.active = 0;
+    S.status = BL_EBREAKDOWN;
+  } else if (S.gnorm <= S.gtol) {
+    S.active = 0;
+  } else if (S.iters >= maxit) {
+    S.active = 0;
+    S.status = BL_ENOCONV;
+  }
+  if (S.active) atomicAdd(flag, 1);
+}
+
+__global__ void k_lb_init(LbArgs a, const int* mask, const double* vals, const double* gn2, const double* ay2,
+                          double l2, double gtol, int relative, int* flag) {
+  const int k = blockIdx.x;
+  if (threadIdx.x != 0) return;
+  LbfgsState& S = a.st[k];
+  if (!mask[k]) {
+    S.active = 0;
+    return;
+  }
+  S.f = vals[k * 3 + 0] + vals[k * 3 + 1] + 0.5 * l2 * vals[k * 3 + 2];
+  S.gnorm = sqrt(gn2[k]);
+  S.gtol = relative ? gtol * 2.0 * sqrt(ay2[k]) : gtol;
+  S.hist_count = 0;
+  S.hist_head = 0;
+  S.gamma = 1.0;
+  S.iters = 0;
+  S.status = BL_OK;
+  S.active = (S.gnorm > S.gtol) ? 1 : 0;
+  if (!isfinite(S.f) || !isfinite(S.gnorm)) {
+    S.active = 0;
+    S.status = BL_EBREAKDOWN;
+  }
+  if (S.active) atomicAdd(flag, 1);
+}
+
+__global__ void k_lb_mask(const LbfgsState* st, int* out, int K) {
+  for (int k = threadIdx.x; k < K; k += blockDim.x) out[k] = st[k].active;
+}
+
+template <typename T>
+static bl_status lbfgs_impl(bl_problem* P, const std::vector<int>& mask_host, const bl_lbfgs_opts* o,
+                            std::vector<bl_solve_info>& info) {
+  const int K = P->K, MH = P->MH;
+  bl_status st = ensure_cpart(P, (size_t)P->n_chunks * 4);
+  if (st != BL_OK) return st;
+  LbArgs a{};
+  a.pairs = P->d_pairs;
+  a.chunks = P->d_chunks;
+  a.st = P->lst;
+  a.MH = MH;
+  a.cpart = P->cpart;
+  a.bcoef = P->dY3;   // K x MH doubles of scratch
+  const int* mask = P->d_active;
+  int* smask = P->d_active + K;
+  T* x = (T*)P->lx;
+  T* g = (T*)P->lg;
+  T* d = (T*)P->ld;
+  T* xt = (T*)P->lxt;
+  T* gt = (T*)P->lgt;
+  T* q = (T*)P->lq;
+  T* Sm = (T*)P->S;
+  T* Ym = (T*)P->Yh;
+  double* vals = P->vals;              // K x 3
+  double* gn2 = P->vals + 3 * K;       // K
+  double* ay2 = P->vals + 4 * K;       // K
+  const double l2 = P->reg.l2_eps;
+  const dim3 cg(P->n_chunks), ct(kChunkThreads);
+
+  // initial value and gradient; ||2 A y|| = ||grad Phi(0)|| for the relative tolerance
+  st = launch_grad(P, x, g, mask, vals);
+  if (st != BL_OK) return st;
+  st = batched_dot(P, g, g, mask, gn2);
+  if (st != BL_OK) return st;
+  if (o->gtol_relative) {
+    st = launch_forward(P, P->y, xt, mask);
+    if (st != BL_OK) return st;
+    st = batched_dot(P, xt, xt, mask, ay2);
+    if (st != BL_OK) return st;
+  }
+  BL_CUDA_TRY(cudaMemsetAsync(P->d_flag, 0, sizeof(int), P->stream));
+  k_lb_init<<<K, 32, 0, P->stream>>>(a, mask, vals, gn2, ay2, l2, o->gtol, o->gtol_relative, P->d_flag);
+  BL_LAUNCH_CHECK(P);
+  BL_CUDA_TRY(cudaMemcpyAsync(P->h_flag, P->d_flag, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+  BL_CUDA_TRY(cudaStreamSynchronize(P->stream));
+  int hist = 0;   // upper bound on any pair's history count
+  for (int it = 0; it < o->max_iters && *P->h_flag > 0; ++it) {
+    // ---- two-loop recursion: q = g; newest to oldest ----
+    const int m = std::min(hist, MH);
+    {
+    ProfScope ps(P, BL_KC_LBFGS);
+    k_lb_step<T><<<cg, ct, 0, P->stream>>>(a, q, g, 0, nullptr, 0, Sm, m > 0 ? 0 : -1, nullptr);
+    BL_LAUNCH_CHECK(P);
+    for (int i = 0; i < m; ++i) {
+      k_lb_coef<<<K, 32, 0, P->stream>>>(a, 0, i);
+      BL_LAUNCH_CHECK(P);
+      k_lb_step<T><<<cg, ct, 0, P->stream>>>(a, q, nullptr, 1, Ym, i, Sm, i + 1 < m ? i + 1 : -1, nullptr);
+      BL_LAUNCH_CHECK(P);
+    }
+    // d = gamma q; oldest to newest
+    k_lb_step<T><<<cg, ct, 0, P->stream>>>(a, q, nullptr, 2, nullptr, 0, Ym, m > 0 ? m - 1 : -1, nullptr);
+    BL_LAUNCH_CHECK(P);
+    for (int i = m - 1; i >= 0; --i) {
+      k_lb_coef<<<K, 32, 0, P->stream>>>(a, 1, i);
+      BL_LAUNCH_CHECK(P);
+      k_lb_step<T><<<cg, ct, 0, P->stream>>>(a, q, nullptr, 3, Sm, i, Ym, i > 0 ? i - 1 : -1, nullptr);
+      BL_LAUNCH_CHECK(P);
+    }
+    // d = -q with g^T d
+    k_lb_step<T><<<cg, ct, 0, P->stream>>>(a, d, q, 0, nullptr, 0, nullptr, -1, nullptr);
+    BL_LAUNCH_CHECK(P);
+    k_lb_step<T><<<cg, ct, 0, P->stream>>>(a, d, nullptr, 4, nullptr, 0, nullptr, -2, g);
+    BL_LAUNCH_CHECK(P);
+    k_lb_coef<<<K, 32, 0, P->stream>>>(a, 2, 0);
+    BL_LAUNCH_CHECK(P);
+    k_lb_restart<T><<<cg, ct, 0, P->stream>>>(a, d, g);
+    BL_LAUNCH_CHECK(P);
+    k_lb_restart_fix<<<K, 32, 0, P->stream>>>(a);
+    BL_LAUNCH_CHECK(P);
+    // ---- backtracking ----
+    k_lb_begin_search<<<K, 32, 0, P->stream>>>(a, smask);
+    BL_LAUNCH_CHECK(P);
+    }
+    for (int bt = 0; bt < std::max(1, o->max_backtrack); ++bt) {
+      {
+        ProfScope ps(P, BL_KC_LBFGS);
+        k_lb_trial<T><<<cg, ct, 0, P->stream>>>(a, smask, xt, x, d);
+        BL_LAUNCH_CHECK(P);
+      }
+      st = launch_grad(P, xt, gt, smask, vals);
+      if (st != BL_OK) return st;
+      BL_CUDA_TRY(cudaMemsetAsync(P->d_flag, 0, sizeof(int), P->stream));
+      k_lb_armijo<<<K, 32, 0, P->stream>>>(a, smask, vals, l2, std::max(1, o->max_backtrack), o->armijo_slack,
+                                            P->d_flag);
+      BL_LAUNCH_CHECK(P);
+      BL_CUDA_TRY(cudaMemcpyAsync(P->h_flag, P->d_flag, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+      BL_CUDA_TRY(cudaStreamSynchronize(P->stream));
+      if (*P->h_flag == 0) break;
+    }
+    // ---- accept ----
+    {
+      ProfScope ps(P, BL_KC_LBFGS);
+      k_lb_accept<T><<<cg, ct, 0, P->stream>>>(a, x, g, xt, gt, Sm, Ym);
+      BL_LAUNCH_CHECK(P);
+      BL_CUDA_TRY(cudaMemsetAsync(P->d_flag, 0, sizeof(int), P->stream));
+      k_lb_post<<<K, 32, 0, P->stream>>>(a, o->max_iters, P->d_flag);
+      BL_LAUNCH_CHECK(P);
+    }
+    BL_CUDA_TRY(cudaMemcpyAsync(P->h_flag, P->d_flag, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+    BL_CUDA_TRY(cudaStreamSynchronize(P->stream));
+    hist = std::min(hist + 1, MH);
+  }
+  std::vector<LbfgsState> hs(K);
+  BL_CUDA_TRY(cudaMemcpyAsync(hs.data(), P->lst, K * sizeof(LbfgsState), cudaMemcpyDeviceToHost, P->stream));
+  BL_CUDA_TRY(cudaStreamSynchronize(P->stream));
+  info.assign(K, bl_solve_info{});
+  for (int k = 0; k < K; ++k) {
+    if (!mask_host[k]) continue;
+    info[k].iters = hs[k].iters;
+    info[k].status = hs[k].status;
+    info[k].resid = hs[k].gnorm;
+    info[k].nsc_est = hs[k].f;
+    info[k].rhs_norm = hs[k].gtol;
+  }
+  return BL_OK;
+}
+
+bl_status run_lower_solve(bl_problem* P, const std::vector<int>& mask_host, const bl_lbfgs_opts* o,
+                          std::vector<bl_solve_info>& info) {
+  return P->prec == BL_FP32 ? lbfgs_impl<float>(P, mask_host, o, info) : lbfgs_impl<double>(P, mask_host, o, info);
+}
+
+}  // namespace bl

@@ -1,0 +1,732 @@
+// Recycle-space refresh (Section 3): Ritz, harmonic Ritz and Ritz generalized singular vectors.
+//
+// For every listed pair with W = [U^(i-1), V^(i-1)] (t = s + k columns):
+//   1. G = W^T W; W~ = W D Q Lambda^{-1/2} from the eigenpairs of the column-scaled Gram,
+//      dropping directions below a relative threshold (orthonormal basis of range(W)).
+//   2. HW~ = H W~ (t' Hessian actions at the current point: the outer form, eq. (3.3)).
+//   3. T = W~^T H W~; for Ritz-GSV also J~ = J W~ (eq. (3.4)), for harmonic Ritz (HW~)^T HW~.
+//   4. Small FP64 problem on one CTA per pair:
+//        Ritz (eq. (3.1))      eigh(T), select smallest / largest / both;
+//        harmonic (eq. (3.2))  (HW~)^T HW~ rho = theta T rho via Cholesky of T;
+//        RGSV (Thm 3.1, eq. (3.4))  mu^2, V_H = eigh(T^{-1} J~^T J~ T^{-1}) (the singular values of
+//        J~ T^{-1}), X = T^{-1} V_H D_H, D_H = diag(1 / sqrt(1 + mu^2)); Z = W~ V_H diag(mu).
+//   5. U~ = W~ Y, C~ = HW~ Y (no new Hessian actions), then C~ = C R by CholeskyQR (twice),
+//      U = U~ R^{-1}, so that C = H U and C^T C = I (Section 2.2.2); Z^T C for the estimate.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "device.cuh"
+
+namespace bl {
+
+constexpr int kGramRows = 32;   // FP32 sub-sum length before the compensated accumulation
+
+// Tall-skinny Gram partials: part[chunk][i * TM + j] = sum_{rows in chunk} A[row][i] B[row][j].
+// FP32 products summed over kGramRows rows, then accumulated as an FP32 (hi, lo) pair with
+// the error-free TwoSum; chunks are combined in FP64 by reduce_units.
+template <typename T>
+__global__ void __launch_bounds__(256) k_ts_gram(const PairDev* pairs, const ChunkDev* chunks, const T* A, int multA,
+                                                 const int* colsA, const T* B, int multB, const int* colsB,
+                                                 const int* mask, int TM, double* part) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const ChunkDev ch = chunks[blockIdx.x];
+  if (mask && !mask[ch.pair]) return;
+  const PairDev pr = pairs[ch.pair];
+  const int ta = colsA[ch.pair], tb = colsB[ch.pair];
+  if (ta == 0 || tb == 0) return;
+  T* As = reinterpret_cast<T*>(smem_raw);               // kGramRows x (TM + 1)
+  T* Bs = As + kGramRows * (TM + 1);
+  const int tid = threadIdx.x;
+  const int nti = (ta + 5) / 6, ntj = (tb + 5) / 6;
+  const bool act = tid < nti * ntj;
+  const int ti = act ? tid / ntj : 0, tj = act ? tid - (tid / ntj) * ntj : 0;
+  float hi[6][6], lo[6][6];
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = 0; j < 6; ++j) hi[i][j] = lo[i][j] = 0.f;
+  const T* Ab = A + pr.off * multA;
+  const T* Bb = B + pr.off * multB;
+  for (int r0 = 0; r0 < ch.len; r0 += kGramRows) {
+    const int nr = min(kGramRows, ch.len - r0);
+    __syncthreads();
+    for (int idx = tid; idx < kGramRows * ta; idx += blockDim.x) {
+      const int c = idx / kGramRows, rr = idx - c * kGramRows;
+      As[rr * (TM + 1) + c] = rr < nr ? Ab[(long long)c * pr.n + ch.start + r0 + rr] : T(0);
+    }
+    for (int idx = tid; idx < kGramRows * tb; idx += blockDim.x) {
+      const int c = idx / kGramRows, rr = idx - c * kGramRows;
+      Bs[rr * (TM + 1) + c] = rr < nr ? Bb[(long long)c * pr.n + ch.start + r0 + rr] : T(0);
+    }
+    __syncthreads();
+    if (!act) continue;
+    float ps[6][6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) ps[i][j] = 0.f;
+    for (int rr = 0; rr < kGramRows; ++rr) {
+      float av[6], bv[6];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        const int ci = 6 * ti + i, cj = 6 * tj + i;
+        av[i] = ci < ta ? (float)As[rr * (TM + 1) + ci] : 0.f;
+        bv[i] = cj < tb ? (float)Bs[rr * (TM + 1) + cj] : 0.f;
+      }
+#pragma unroll
+      for (int i = 0; i < 6; ++i)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) ps[i][j] = fmaf(av[i], bv[j], ps[i][j]);
+    }
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+#pragma unroll
+      for (int j = 0; j < 6; ++j) {
+        // TwoSum(hi, ps): exact sum s + err
+        const float s = hi[i][j] + ps[i][j];
+        const float bb = s - hi[i][j];
+        const float err = (hi[i][j] - (s - bb)) + (ps[i][j] - bb);
+        hi[i][j] = s;
+        lo[i][j] += err;
+      }
+  }
+  if (!act) return;
+  double* out = part + (size_t)blockIdx.x * TM * TM;
+#pragma unroll
+  for (int i = 0; i < 6; ++i)
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+      const int ci = 6 * ti + i, cj = 6 * tj + j;
+      if (ci < ta && cj < tb) out[ci * TM + cj] = (double)hi[i][j] + (double)lo[i][j];
+    }
+}
+
+// Double-precision variant for FP64 problems: plain FP64 accumulation.
+template <>
+__global__ void __launch_bounds__(256) k_ts_gram<double>(const PairDev* pairs, const ChunkDev* chunks, const double* A,
+                                                         int multA, const int* colsA, const double* B, int multB,
+                                                         const int* colsB, const int* mask, int TM, double* part) {
+  const ChunkDev ch = chunks[blockIdx.x];
+  if (mask && !mask[ch.pair]) return;
+  const PairDev pr = pairs[ch.pair];
+  const int ta = colsA[ch.pair], tb = colsB[ch.pair];
+  const double* Ab = A + pr.off * multA;
+  const double* Bb = B + pr.off * multB;
+  double* out = part + (size_t)blockIdx.x * TM * TM;
+  for (int e = threadIdx.x; e < ta * tb; e += blockDim.x) {
+    const int i = e / tb, j = e - (e / tb) * tb;
+    double s = 0.0;
+    for (int r = 0; r < ch.len; ++r)
+      s += Ab[(long long)i * pr.n + ch.start + r] * Bb[(long long)j * pr.n + ch.start + r];
+    out[i * TM + j] = s;
+  }
+}
+
+// out[row][j] = sum_l A[row][l] M[l][j]   (M: ta x tb, FP64, ld TM); in place allowed (out == A).
+template <typename T>
+__global__ void __launch_bounds__(256) k_ts_gemm(const PairDev* pairs, const ChunkDev* chunks, const T* A, int multA,
+                                                 const int* colsA, const double* M, int TM, T* out, int multO,
+                                                 const int* colsO, const int* mask) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const ChunkDev ch = chunks[blockIdx.x];
+  if (mask && !mask[ch.pair]) return;
+  const PairDev pr = pairs[ch.pair];
+  const int ta = colsA[ch.pair], tb = colsO[ch.pair];
+  if (tb == 0) return;
+  T* Ms = reinterpret_cast<T*>(smem_raw);        // ta x tb
+  T* As = Ms + TM * TM;                          // 64 rows x (ta + 1)
+  const double* Mk = M + (size_t)ch.pair * TM * TM;
+  for (int idx = threadIdx.x; idx < ta * tb; idx += blockDim.x) {
+    const int l = idx / tb, j = idx - (idx / tb) * tb;
+    Ms[l * tb + j] = (T)Mk[l * TM + j];
+  }
+  const T* Ab = A + pr.off * multA;
+  T* Ob = out + pr.off * multO;
+  const int ngrp = (tb + 23) / 24;
+  for (int r0 = 0; r0 < ch.len; r0 += 64) {
+    const int nr = min(64, ch.len - r0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 64 * ta; idx += blockDim.x) {
+      const int l = idx / 64, rr = idx - l * 64;
+      As[rr * (ta + 1) + l] = rr < nr ? Ab[(long long)l * pr.n + ch.start + r0 + rr] : T(0);
+    }
+    __syncthreads();
+    for (int job = threadIdx.x; job < 64 * ngrp; job += blockDim.x) {
+      const int rr = job & 63, grp = job >> 6;
+      if (rr >= nr) continue;
+      T acc[24];
+#pragma unroll
+      for (int j = 0; j < 24; ++j) acc[j] = T(0);
+      for (int l = 0; l < ta; ++l) {
+        const T av = As[rr * (ta + 1) + l];
+#pragma unroll
+        for (int j = 0; j < 24; ++j) {
+          const int cj = grp * 24 + j;
+          if (cj < tb) acc[j] = fma(av, Ms[l * tb + cj], acc[j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 24; ++j) {
+        const int cj = grp * 24 + j;
+        if (cj < tb) Ob[(long long)cj * pr.n + ch.start + r0 + rr] = acc[j];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Small dense FP64 linear algebra, one CTA per pair.
+
+// Parallel cyclic Jacobi (round-robin pairing) on symmetric n x n A (ld n), eigenvectors in V.
+// On return A's diagonal holds the eigenvalues; w (ascending) and V's columns are sorted.
+__device__ void dev_jacobi(double* A, double* V, int n, double* w, double* cs, int* perm) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int idx = tid; idx < n * n; idx += nt) V[idx] = (idx / n == idx % n) ? 1.0 : 0.0;
+  __syncthreads();
+  if (n <= 1) {
+    if (tid == 0 && n == 1) { w[0] = A[0]; perm[0] = 0; }
+    __syncthreads();
+    return;
+  }
+  const int m = n + (n & 1);
+  __shared__ double offs, dias;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    if (tid == 0) { offs = 0.0; dias = 0.0; }
+    __syncthreads();
+    double lo = 0.0, ld = 0.0;
+    for (int idx = tid; idx < n * n; idx += nt) {
+      const int i = idx / n, j = idx - (idx / n) * n;
+      if (i == j) ld += A[idx] * A[idx];
+      else lo += A[idx] * A[idx];
+    }
+    lo = warp_sum(lo);
+    ld = warp_sum(ld);
+    if ((tid & 31) == 0) { atomicAdd(&offs, lo); atomicAdd(&dias, ld); }
+    __syncthreads();
+    const bool done = !(offs > 1e-30 * dias) || offs == 0.0;
+    __syncthreads();
+    if (done) break;
+    for (int rnd = 0; rnd < m - 1; ++rnd) {
+      // rotation parameters for the m/2 disjoint pairs of this round
+      for (int i = tid; i < m / 2; i += nt) {
+        int p, q;
+        if (i == 0) { p = rnd; q = m - 1; }
+        else { p = (rnd + i) % (m - 1); q = (rnd - i + m - 1) % (m - 1); }
+        if (p > q) { const int t = p; p = q; q = t; }
+        double c = 1.0, s = 0.0;
+        if (q < n) {
+          const double apq = A[p * n + q];
+          if (fabs(apq) > 1e-300) {
+            const double th = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+            const double t = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            s = t * c;
+          }
+        }
+        cs[4 * i] = c; cs[4 * i + 1] = s; cs[4 * i + 2] = p; cs[4 * i + 3] = q;
+      }
+      __syncthreads();
+      // rows: A <- J^T A
+      for (int idx = tid; idx < (m / 2) * n; idx += nt) {
+        const int i = idx / n, j = idx - (idx / n) * n;
+        const int p = (int)cs[4 * i + 2], q = (int)cs[4 * i + 3];
+        if (q >= n) continue;
+        const double c = cs[4 * i], s = cs[4 * i + 1];
+        const double ap = A[p * n + j], aq = A[q * n + j];
+        A[p * n + j] = c * ap - s * aq;
+        A[q * n + j] = s * ap + c * aq;
+      }
+      __syncthreads();
+      // columns: A <- A J, V <- V J
+      for (int idx = tid; idx < (m / 2) * n; idx += nt) {
+        const int i = idx / n, j = idx - (idx / n) * n;
+        const int p = (int)cs[4 * i + 2], q = (int)cs[4 * i + 3];
+        if (q >= n) continue;
+        const double c = cs[4 * i], s = cs[4 * i + 1];
+        const double ap = A[j * n + p], aq = A[j * n + q];
+        A[j * n + p] = c * ap - s * aq;
+        A[j * n + q] = s * ap + c * aq;
+        const double vp = V[j * n + p], vq = V[j * n + q];
+        V[j * n + p] = c * vp - s * vq;
+        V[j * n + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+    }
+  }
+  // sort ascending (ties by index)
+  if (tid == 0) {
+    for (int i = 0; i < n; ++i) perm[i] = i;
+    for (int i = 1; i < n; ++i) {
+      const int pi = perm[i];
+      const double v = A[pi * n + pi];
+      int j = i - 1;
+      while (j >= 0 && A[perm[j] * n + perm[j]] > v) { perm[j + 1] = perm[j]; --j; }
+      perm[j + 1] = pi;
+    }
+    for (int i = 0; i < n; ++i) w[i] = A[perm[i] * n + perm[i]];
+  }
+  __syncthreads();
+}
+
+// In-place lower Cholesky of SPD n x n A (ld lda); returns false (in every thread) if not SPD.
+__device__ bool dev_cholesky(double* A, int n, int lda) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) ok = 1;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      double d = A[j * lda + j];
+      for (int k = 0; k < j; ++k) d -= A[j * lda + k] * A[j * lda + k];
+      if (!(d > 0.0)) { ok = 0; d = 1.0; }
+      A[j * lda + j] = sqrt(d);
+    }
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) {
+      double v = A[i * lda + j];
+      for (int k = 0; k < j; ++k) v -= A[i * lda + k] * A[j * lda + k];
+      A[i * lda + j] = v / A[j * lda + j];
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, j = idx - (idx / n) * n;
+    if (j > i) A[i * lda + j] = 0.0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Solve L L^T X = B in place (L lower, ld lda; B n x nrhs, ld ldb), one thread per column.
+__device__ void dev_chol_solve(const double* L, int n, int lda, double* B, int nrhs, int ldb) {
+  for (int c = threadIdx.x; c < nrhs; c += blockDim.x) {
+    for (int i = 0; i < n; ++i) {
+      double v = B[i * ldb + c];
+      for (int k = 0; k < i; ++k) v -= L[i * lda + k] * B[k * ldb + c];
+      B[i * ldb + c] = v / L[i * lda + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double v = B[i * ldb + c];
+      for (int k = i + 1; k < n; ++k) v -= L[k * lda + i] * B[k * ldb + c];
+      B[i * ldb + c] = v / L[i * lda + i];
+    }
+  }
+  __syncthreads();
+}
+
+// Indices selected from ascending values: smallest s, largest s, or both halves (Table 1).
+__device__ __forceinline__ int sel_index(int n, int s, int which, int j) {
+  if (which == BL_SIZE_SMALL) return j;
+  if (which == BL_SIZE_LARGE) return n - s + j;
+  const int lo = s - s / 2;
+  return j < lo ? j : n - (s - j);
+}
+
+struct DenseArgs {
+  int TM, p;
+  double* G;     // K x TM x TM: W^T W   -> scratch
+  double* T;     // K x TM x TM: W~^T H W~
+  double* GH;    // K x TM x TM: (HW~)^T HW~
+  const double* J;  // K x TM x p: J W~ ([k][col][m])
+  double* Y;     // K x TM x TM: coefficient outputs
+  double* Y2;    // K x TM x TM
+  double* scratch;  // K x 4 x TM x TM
+  int* tk;       // reduced basis size per pair (in/out)
+  int* snew;     // selected size per pair (out)
+  const int* mask;
+  int kind, size, side, s;
+  double drop;   // relative eigenvalue threshold of the orthonormalisation
+};
+
+// 1. G (t x t) -> B1 (t x t'): orthonormal-basis coefficients
+__global__ void k_dense_orth(DenseArgs a, const int* tcols) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int k = blockIdx.x;
+  if (!a.mask[k]) return;
+  const int t = tcols[k], TM = a.TM;
+  double* As = reinterpret_cast<double*>(smem_raw);
+  double* Vs = As + TM * TM;
+  double* w = Vs + TM * TM;
+  double* dsc = w + TM;
+  double* cs = dsc + TM;                  // 4 * TM / 2
+  int* perm = reinterpret_cast<int*>(cs + 2 * TM + 4);
+  const double* G = a.G + (size_t)k * TM * TM;
+  for (int i = threadIdx.x; i < t; i += blockDim.x) {
+    const double d = G[i * TM + i];
+    dsc[i] = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < t * t; idx += blockDim.x) {
+    const int i = idx / t, j = idx - (idx / t) * t;
+    As[idx] = 0.5 * (G[i * TM + j] + G[j * TM + i]) * dsc[i] * dsc[j];
+  }
+  __syncthreads();
+  dev_jacobi(As, Vs, t, w, cs, perm);
+  __shared__ int keep0, nkeep;
+  if (threadIdx.x == 0) {
+    const double wmax = t > 0 ? w[t - 1] : 0.0;
+    int k0 = 0;
+    while (k0 < t && !(w[k0] > a.drop * wmax)) ++k0;
+    keep0 = k0;
+    nkeep = t - k0;
+    a.tk[k] = t - k0;
+  }
+  __syncthreads();
+  double* Y = a.Y + (size_t)k * TM * TM;   // t x t'
+  for (int idx = threadIdx.x; idx < t * nkeep; idx += blockDim.x) {
+    const int i = idx / nkeep, j = idx - (idx / nkeep) * nkeep;
+    const int ev = perm[keep0 + j];
+    Y[i * TM + j] = dsc[i] * Vs[i * t + ev] / sqrt(w[keep0 + j]);
+  }
+}
+
+// 2. selection: Y (t' x s) recycle coefficients, Y2 (t' x s) NSC coefficients
+__global__ void k_dense_select(DenseArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int k = blockIdx.x;
+  if (!a.mask[k]) return;
+  const int TM = a.TM, t = a.tk[k];
+  double* As = reinterpret_cast<double*>(smem_raw);
+  double* Vs = As + TM * TM;
+  double* w = Vs + TM * TM;
+  double* cs = w + TM;
+  int* perm = reinterpret_cast<int*>(cs + 2 * TM + 4);
+  double* T = a.T + (size_t)k * TM * TM;
+  double* Y = a.Y + (size_t)k * TM * TM;
+  double* Y2 = a.Y2 + (size_t)k * TM * TM;
+  double* S1 = a.scratch + (size_t)k * 4 * TM * TM;   // t x t scratch
+  double* S2 = S1 + TM * TM;
+  __shared__ int s_sel;
+  if (threadIdx.x == 0) {
+    int s = min(a.s, t);
+    if (a.kind == BL_RECYCLE_RGSV) s = min(s, a.p);
+    s_sel = s;
+    a.snew[k] = s;
+  }
+  // symmetrise T
+  for (int idx = threadIdx.x; idx < t * t; idx += blockDim.x) {
+    const int i = idx / t, j = idx - (idx / t) * t;
+    S1[i * TM + j] = 0.5 * (T[i * TM + j] + T[j * TM + i]);
+  }
+  __syncthreads();
+  const int s = s_sel;
+  if (s == 0) return;
+  if (a.kind == BL_RECYCLE_RITZ) {
+    for (int idx = threadIdx.x; idx < t * t; idx += blockDim.x) As[idx] = S1[(idx / t) * TM + idx % t];
+    __syncthreads();
+    dev_jacobi(As, Vs, t, w, cs, perm);
+    for (int idx = threadIdx.x; idx < t * s; idx += blockDim.x) {
+      const int i = idx / s, j = idx - (idx / s) * s;
+      Y[i * TM + j] = Vs[i * t + perm[sel_index(t, s, a.size, j)]];
+    }
+    return;
+  }
+  // Cholesky of T in S1 (lower)
+  const bool ok = dev_cholesky(S1, t, TM);
+  if (!ok) {
+    if (threadIdx.x == 0) a.snew[k] = -1;   // not SPD: reported as breakdown by the host
+    return;
+  }
+  if (a.kind == BL_RECYCLE_HRITZ) {
+    // M = L^{-1} GH L^{-T}: solve with columns, then rows
+    const double* GH = a.GH + (size_t)k * TM * TM;
+    for (int idx = threadIdx.x; idx < t * t; idx += blockDim.x) {
+      const int i = idx / t, j = idx - (idx / t) * t;
+      S2[i * TM + j] = 0.5 * (GH[i * TM + j] + GH[j * TM + i]);
+    }
+    __syncthreads();
+    // forward solve L X = GH (columns), then L M^T = X^T
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int c = threadIdx.x; c < t; c += blockDim.x)
+        for (int i = 0; i < t; ++i) {
+          double v = S2[i * TM + c];
+          for (int kk = 0; kk < i; ++kk) v -= S1[i * TM + kk] * S2[kk * TM + c];
+          S2[i * TM + c] = v / S1[i * TM + i];
+        }
+      __syncthreads();
+      // transpose S2 in place
+      for (int idx = threadIdx.x; idx < t * t; idx += blockDim.x) {
+        const int i = idx / t, j = idx - (idx / t) * t;
+        if (i < j) { const double x = S2[i * TM + j]; S2[i * TM + j] = S2[j * TM + i]; S2[j * TM + i] = x; }
+      }
+      __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < t * t; idx += blockDim.x) {
+      const int i = idx / t, j = idx - (idx / t) * t;
+      As[idx] = 0.5 * (S2[i * TM + j] + S2[j * TM + i]);
+    }
+    __syncthreads();
+    dev_jacobi(As, Vs, t, w, cs, perm);
+    // rho = L^{-T} y for the selected eigenvectors
+    for (int idx = threadIdx.x; idx < t * s; idx += blockDim.x) {
+      const int i = idx / s, j = idx - (idx / s) * s;
+      Y[i * TM + j] = Vs[i * t + perm[sel_index(t, s, a.size, j)]];
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < s; c += blockDim.x)
+      for (int i = t - 1; i >= 0; --i) {
+        double v = Y[i * TM + c];
+        for (int kk = i + 1; kk < t; ++kk) v -= S1[kk * TM + i] * Y[kk * TM + c];
+        Y[i * TM + c] = v / S1[i * TM + i];
+      }
+    return;
+  }
+  // RGSV: F = J~^T J~ (t x t) into S2, M = T^{-1} F T^{-1}
+  const double* J = a.J + (size_t)k * TM * a.p;
+  for (int idx = threadIdx.x; idx < t * t; idx += blockDim.x) {
+    const int i = idx / t, j = idx - (idx / t) * t;
+    if (j < i) continue;
+    double v = 0.0;
+    for (int m = 0; m < a.p; ++m) v += J[(size_t)i * a.p + m] * J[(size_t)j * a.p + m];
+    S2[i * TM + j] = v;
+    S2[j * TM + i] = v;
+  }
+  __syncthreads();
+  dev_chol_solve(S1, t, TM, S2, t, TM);        // S2 = T^{-1} F
+  for (int idx = threadIdx.x; idx < t * t; idx += blockDim.x) {
+    const int i = idx / t, j = idx - (idx / t) * t;
+    if (i < j) { const double x = S2[i * TM + j]; S2[i * TM + j] = S2[j * TM + i]; S2[j * TM + i] = x; }
+  }
+  __syncthreads();
+  dev_chol_solve(S1, t, TM, S2, t, TM);        // S2 = T^{-1} (T^{-1} F)^T = T^{-1} F T^{-1}
+  for (int idx = threadIdx.x; idx < t * t; idx += blockDim.x) {
+    const int i = idx / t, j = idx - (idx / t) * t;
+    As[idx] = 0.5 * (S2[i * TM + j] + S2[j * TM + i]);
+  }
+  __syncthreads();
+  dev_jacobi(As, Vs, t, w, cs, perm);          // ascending mu^2, V_H
+  // V_H,sel into Y2 (scaled by mu later), X_sel = T^{-1} V_H,sel D_H into Y
+  for (int idx = threadIdx.x; idx < t * s; idx += blockDim.x) {
+    const int i = idx / s, j = idx - (idx / s) * s;
+    const int e = sel_index(t, s, a.size, j);
+    const double vh = Vs[i * t + perm[e]];
+    Y2[i * TM + j] = vh;
+    Y[i * TM + j] = vh;
+  }
+  __syncthreads();
+  dev_chol_solve(S1, t, TM, Y, s, TM);         // Y = T^{-1} V_H,sel
+  for (int idx = threadIdx.x; idx < t * s; idx += blockDim.x) {
+    const int i = idx / s, j = idx - (idx / s) * s;
+    const int e = sel_index(t, s, a.size, j);
+    const double mu = sqrt(fmax(w[e], 0.0));
+    const double dh = 1.0 / sqrt(1.0 + mu * mu);
+    const double x = Y[i * TM + j] * dh;
+    const double vh = Y2[i * TM + j];
+    if (a.side == BL_SIDE_RIGHT) Y[i * TM + j] = x;
+    else if (a.side == BL_SIDE_LEFT) Y[i * TM + j] = vh;
+    else Y[i * TM + j] = 0.5 * (vh + x);
+    Y2[i * TM + j] = vh * mu;
+  }
+}
+
+// 3. CholeskyQR step: S = C~^T C~ (s x s) -> Rinv (upper inverse of the Cholesky factor R^T = L)
+__global__ void k_dense_cholinv(DenseArgs a, const int* scols, double* G, double* Rinv) {
+  const int k = blockIdx.x;
+  if (!a.mask[k]) return;
+  const int TM = a.TM, s = scols[k];
+  if (s <= 0) return;
+  double* S = G + (size_t)k * TM * TM;
+  double* R = Rinv + (size_t)k * TM * TM;
+  for (int idx = threadIdx.x; idx < s * s; idx += blockDim.x) {
+    const int i = idx / s, j = idx - (idx / s) * s;
+    if (i < j) { const double v = 0.5 * (S[i * TM + j] + S[j * TM + i]); S[i * TM + j] = v; S[j * TM + i] = v; }
+  }
+  __syncthreads();
+  if (!dev_cholesky(S, s, TM)) {
+    if (threadIdx.x == 0) a.snew[k] = -1;
+    return;
+  }
+  // C = C~ L^{-T}: Rinv = L^{-T} (upper); column c of L^{-T} solves L^T x = e_c
+  for (int c = threadIdx.x; c < s; c += blockDim.x) {
+    for (int i = s - 1; i >= 0; --i) {
+      double v = (i == c) ? 1.0 : 0.0;
+      for (int kk = i + 1; kk < s; ++kk) v -= S[kk * TM + i] * R[kk * TM + c];
+      R[i * TM + c] = v / S[i * TM + i];
+    }
+  }
+}
+
+__global__ void k_copy_ztc(const int* mask, const int* scols, const double* G, int TM, int SMAX, double* ztc,
+                           int K) {
+  const int k = blockIdx.x;
+  if (!mask[k]) return;
+  const int s = scols[k];
+  for (int idx = threadIdx.x; idx < SMAX * SMAX; idx += blockDim.x) {
+    const int i = idx / SMAX, j = idx - (idx / SMAX) * SMAX;
+    ztc[(size_t)k * SMAX * SMAX + idx] = (i < s && j < s) ? G[(size_t)k * TM * TM + i * TM + j] : 0.0;
+  }
+}
+
+template <typename T>
+static bl_status gram(bl_problem* P, const void* A, int multA, const int* colsA, const void* B, int multB,
+                      const int* colsB, const int* mask, double* out) {
+  const int TM = P->TM;
+  bl_status st = ensure_cpart(P, (size_t)P->n_chunks * TM * TM);
+  if (st != BL_OK) return st;
+  // entries of pairs with fewer columns than TM stay unwritten: clear the partials first
+  ProfScope ps(P, BL_KC_GRAM);
+  BL_CUDA_TRY(cudaMemsetAsync(P->cpart, 0, (size_t)P->n_chunks * TM * TM * sizeof(double), P->stream));
+  const size_t sm = 2 * (size_t)kGramRows * (TM + 1) * sizeof(T);
+  BL_CUDA_TRY(cudaFuncSetAttribute(k_ts_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_ts_gram<T><<<P->n_chunks, 256, sm, P->stream>>>(P->d_pairs, P->d_chunks, (const T*)A, multA, colsA,
+                                                    (const T*)B, multB, colsB, mask, TM, P->cpart);
+  BL_LAUNCH_CHECK(P);
+  return reduce_units(P, P->cpart, TM * TM, 1, false, mask, nullptr, out);
+}
+
+template <typename T>
+static bl_status gemm(bl_problem* P, const void* A, int multA, const int* colsA, const double* M, void* out,
+                      int multO, const int* colsO, const int* mask) {
+  const int TM = P->TM;
+  const size_t sm = ((size_t)TM * TM + 64 * (TM + 1)) * sizeof(T);
+  ProfScope ps(P, BL_KC_GEMM);
+  BL_CUDA_TRY(cudaFuncSetAttribute(k_ts_gemm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  k_ts_gemm<T><<<P->n_chunks, 256, sm, P->stream>>>(P->d_pairs, P->d_chunks, (const T*)A, multA, colsA, M, TM,
+                                                    (T*)out, multO, colsO, mask);
+  BL_LAUNCH_CHECK(P);
+  return BL_OK;
+}
+
+template <typename T>
+static bl_status refresh_impl(bl_problem* P, const std::vector<int>& mask_host, const bl_recycle_opts* o) {
+  const int K = P->K, TM = P->TM;
+  std::vector<int> msk(K, 0), tcols(K, 0);
+  bool any = false;
+  for (int k = 0; k < K; ++k) {
+    if (!mask_host[k]) continue;
+    const int t = P->s_k[k] + P->kb_k[k];
+    if (t == 0) continue;            // no basis yet: the recycle space stays empty
+    msk[k] = 1;
+    tcols[k] = t;
+    any = true;
+  }
+  if (!any) return BL_OK;
+  int* d_mask = P->d_active + 2 * K;      // refresh mask
+  int* d_t = P->d_cols;                   // t per pair
+  int* d_tk = P->d_tk;                    // t' per pair
+  int* d_sn = P->d_tk + K;                // selected s per pair
+  BL_CUDA_TRY(cudaMemcpyAsync(d_mask, msk.data(), K * sizeof(int), cudaMemcpyHostToDevice, P->stream));
+  BL_CUDA_TRY(cudaMemcpyAsync(d_t, tcols.data(), K * sizeof(int), cudaMemcpyHostToDevice, P->stream));
+  // 0. W = [U, V]
+  for (int k = 0; k < K; ++k) {
+    if (!msk[k]) continue;
+    const auto& ph = P->ph[k];
+    char* Wk = (char*)P->W + ph.off * TM * P->esz;
+    if (P->s_k[k])
+      BL_CUDA_TRY(cudaMemcpyAsync(Wk, (const char*)P->U + ph.off * P->SMAX * P->esz, (size_t)P->s_k[k] * ph.n * P->esz,
+                                  cudaMemcpyDeviceToDevice, P->stream));
+    if (P->kb_k[k])
+      BL_CUDA_TRY(cudaMemcpyAsync(Wk + (size_t)P->s_k[k] * ph.n * P->esz, (const char*)P->V + ph.off * P->KMAX * P->esz,
+                                  (size_t)P->kb_k[k] * ph.n * P->esz, cudaMemcpyDeviceToDevice, P->stream));
+  }
+  DenseArgs da{};
+  da.TM = TM;
+  da.p = P->p;
+  da.G = P->dG;
+  da.T = P->dT;
+  da.GH = P->dT + (size_t)K * TM * TM;
+  da.J = P->dJ;
+  da.Y = P->dY;
+  da.Y2 = P->dY2;
+  da.scratch = P->dY3;
+  da.tk = d_tk;
+  da.snew = d_sn;
+  da.mask = d_mask;
+  da.kind = o->kind;
+  da.size = o->size;
+  da.side = o->side;
+  da.s = o->s;
+  da.drop = P->prec == BL_FP32 ? 1e-6 : 1e-12;
+  const size_t dsm = (2 * (size_t)TM * TM + 4 * TM + 8) * sizeof(double) + TM * sizeof(int) + 64;
+  BL_CUDA_TRY(cudaFuncSetAttribute(k_dense_orth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+  BL_CUDA_TRY(cudaFuncSetAttribute(k_dense_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+
+  // 1. orthonormal basis W~ = W B1
+  bl_status st = gram<T>(P, P->W, TM, d_t, P->W, TM, d_t, d_mask, P->dG);
+  if (st != BL_OK) return st;
+  {
+    ProfScope ps(P, BL_KC_DENSE);
+    k_dense_orth<<<K, 256, dsm, P->stream>>>(da, d_t);
+    BL_LAUNCH_CHECK(P);
+  }
+  st = gemm<T>(P, P->W, TM, d_t, P->dY, P->Wt, TM, d_tk, d_mask);
+  if (st != BL_OK) return st;
+  // 2. H W~
+  BL_CUDA_TRY(cudaMemcpyAsync(P->d_cols, d_tk, K * sizeof(int), cudaMemcpyDeviceToDevice, P->stream));
+  int tmax = 0;
+  for (int k = 0; k < K; ++k) tmax = std::max(tmax, tcols[k]);
+  st = launch_hvp(P, P->Wt, P->HWt, TM, tmax, d_mask, nullptr, nullptr);
+  if (st != BL_OK) return st;
+  // 3. projected matrices
+  st = gram<T>(P, P->Wt, TM, d_tk, P->HWt, TM, d_tk, d_mask, P->dT);
+  if (st != BL_OK) return st;
+  if (o->kind == BL_RECYCLE_HRITZ) {
+    st = gram<T>(P, P->HWt, TM, d_tk, P->HWt, TM, d_tk, d_mask, P->dT + (size_t)K * TM * TM);
+    if (st != BL_OK) return st;
+  }
+  if (o->kind == BL_RECYCLE_RGSV) {
+    st = launch_jw(P, P->Wt, TM, tmax, d_mask, P->dJ);
+    if (st != BL_OK) return st;
+  }
+  // 4. selection
+  {
+    ProfScope ps(P, BL_KC_DENSE);
+    k_dense_select<<<K, 256, dsm, P->stream>>>(da);
+    BL_LAUNCH_CHECK(P);
+  }
+  // 5. U~ = W~ Y, C~ = HW~ Y, Z = W~ Y2
+  st = gemm<T>(P, P->Wt, TM, d_tk, P->dY, P->U, P->SMAX, d_sn, d_mask);
+  if (st != BL_OK) return st;
+  st = gemm<T>(P, P->HWt, TM, d_tk, P->dY, P->C, P->SMAX, d_sn, d_mask);
+  if (st != BL_OK) return st;
+  if (o->kind == BL_RECYCLE_RGSV) {
+    st = gemm<T>(P, P->Wt, TM, d_tk, P->dY2, P->Z, P->SMAX, d_sn, d_mask);
+    if (st != BL_OK) return st;
+  }
+  // CholeskyQR2 of C~, applied to U~ as well
+  for (int rep = 0; rep < 2; ++rep) {
+    st = gram<T>(P, P->C, P->SMAX, d_sn, P->C, P->SMAX, d_sn, d_mask, P->dG);
+    if (st != BL_OK) return st;
+    {
+      ProfScope ps(P, BL_KC_DENSE);
+      k_dense_cholinv<<<K, 128, 0, P->stream>>>(da, d_sn, P->dG, P->dY);
+      BL_LAUNCH_CHECK(P);
+    }
+    st = gemm<T>(P, P->C, P->SMAX, d_sn, P->dY, P->C, P->SMAX, d_sn, d_mask);
+    if (st != BL_OK) return st;
+    st = gemm<T>(P, P->U, P->SMAX, d_sn, P->dY, P->U, P->SMAX, d_sn, d_mask);
+    if (st != BL_OK) return st;
+  }
+  if (o->kind == BL_RECYCLE_RGSV) {
+    st = gram<T>(P, P->Z, P->SMAX, d_sn, P->C, P->SMAX, d_sn, d_mask, P->dG);
+    if (st != BL_OK) return st;
+    k_copy_ztc<<<K, 128, 0, P->stream>>>(d_mask, d_sn, P->dG, TM, P->SMAX, P->ztc, K);
+    BL_LAUNCH_CHECK(P);
+  }
+  std::vector<int> sn(K, 0);
+  BL_CUDA_TRY(cudaMemcpyAsync(sn.data(), d_sn, K * sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+  BL_CUDA_TRY(cudaStreamSynchronize(P->stream));
+  bool broke = false;
+  for (int k = 0; k < K; ++k) {
+    if (!msk[k]) continue;
+    if (sn[k] < 0) {
+      broke = true;
+      P->s_k[k] = 0;
+      P->hz_k[k] = 0;
+    } else {
+      P->s_k[k] = sn[k];
+      P->hz_k[k] = (o->kind == BL_RECYCLE_RGSV && sn[k] > 0) ? 1 : 0;
+    }
+    P->kb_k[k] = 0;   // the basis has been consumed
+  }
+  BL_CUDA_TRY(cudaMemcpyAsync(P->d_s, P->s_k.data(), K * sizeof(int), cudaMemcpyHostToDevice, P->stream));
+  BL_CUDA_TRY(cudaMemcpyAsync(P->d_hasz, P->hz_k.data(), K * sizeof(int), cudaMemcpyHostToDevice, P->stream));
+  if (broke) return fail(BL_EBREAKDOWN, "recycle refresh: projected Hessian not positive definite");
+  return BL_OK;
+}
+
+bl_status run_ritz_update(bl_problem* P, const std::vector<int>& mask_host, const bl_recycle_opts* o) {
+  return P->prec == BL_FP32 ? refresh_impl<float>(P, mask_host, o) : refresh_impl<double>(P, mask_host, o);
+}
+
+}  // namespace bl

@@ -123,9 +123,11 @@ def foe_256() -> Workload:
     return _fill(wl, _cfg_seed(1))
 
 
-def batch_64() -> Workload:
-    """64 pairs of uneven square sizes, FoE with 16 5x5 filters (p = 416), recycle dim 16."""
-    ss = _cfg_seed(2)
+def batch_64(replica: int = 0) -> Workload:
+    """64 pairs of uneven square sizes, FoE with 16 5x5 filters (p = 416), recycle dim 16.
+
+    replica > 0 draws an independent batch of the same recipe (one per data-parallel rank)."""
+    ss = _cfg_seed(2) if replica == 0 else np.random.SeedSequence([ROOT_SEED, 2, replica])
     meta_ss, data_ss = ss.spawn(2)
     rng = np.random.default_rng(meta_ss)
     sides = [128, 192, 256, 384, 512]

@@ -1,0 +1,168 @@
+"""GPU parity of the solvers: plain and recycled CG, the recycle refresh, the L-BFGS lower
+solve and the full hypergradient, against the FP64 checker on the same inputs.
+
+Bars: FP64 runs follow the checker's iteration counts within one iteration and agree to
+1e-8; FP32 runs reach hypergradients within 1e-4 relative error of the checker's
+high-accuracy reference (the stated bar for hypergradients)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2412_08264_gb300 import synth
+from oracle import recycle as orc
+from oracle.krylov import rcg
+from tests.gpu_util import DEV, make, packed, r32, rel, split
+
+pytestmark = pytest.mark.gpu
+
+
+def lower_points(prob, th, gtol=1e-9):
+    xs, _ = prob.solve_lower(th, gtol=gtol)
+    return xs
+
+
+def small_wl(sizes=((48, 52), (33, 70)), N=3, f=5, rb=2, seed=1):
+    return synth.uneven_foe(list(sizes), n_filters=N, f=f, blur_radius=rb, seed=seed)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_plain_cg_matches_checker(precision):
+    wl = small_wl()
+    P, prob, dt = make(wl, precision, max_recycle=4, max_basis=60)
+    th = r32(wl.theta0) if precision == "fp32" else wl.theta0
+    xs = [r32(x) for x in lower_points(prob, th)] if precision == "fp32" else lower_points(prob, th)
+    P.set_point(torch.tensor(th, dtype=torch.float64, device=DEV), packed(xs, dt))
+    w = P.zeros()
+    tol = 1e-8 if precision == "fp64" else 1e-6
+    info = P.hessian_solve(w, recycle=False, tol=tol, relative=True, maxit=3000)
+    ws = split(w, P.sizes)
+    hg = P.hypergrad(w, per_pair=True)[1].cpu().numpy()
+    for k in range(P.K):
+        g = prob.rhs(k, xs[k])
+        out = rcg(prob.apply_H(k, xs[k], th), g, np.zeros_like(g), None, None, tol=tol * np.linalg.norm(g),
+                  maxit=3000)
+        wref = prob.reference_w(k, xs[k], th)
+        hg_ref = prob.Jw(k, xs[k], th, wref)
+        if precision == "fp64":
+            assert abs(info[k]["iters"] - out["iters"]) <= 1, (info[k]["iters"], out["iters"])
+            assert rel(ws[k], out["w"]) < 1e-8
+        assert rel(hg[k], hg_ref) < 1e-4, rel(hg[k], hg_ref)
+
+
+def test_recycled_sequence_fp64_matches_checker():
+    """Three systems along a theta path, RGen-L(R) refresh between them: the GPU's recycled CG
+    takes the checker's iteration counts (+-1) and reaches the same hypergradients."""
+    wl = small_wl(sizes=((40, 44),), N=3, seed=4)
+    P, prob, dt = make(wl, "fp64", max_recycle=6, max_basis=60)
+    th = wl.theta0.copy()
+    rng = np.random.default_rng(0)
+    U = C = Z = None
+    V = None
+    w_prev = None
+    s = 6
+    for i in range(3):
+        xs = lower_points(prob, th, gtol=1e-10)
+        x = xs[0]
+        theta = torch.tensor(th, dtype=torch.float64, device=DEV)
+        P.set_point(theta, packed(xs, dt))
+        AH = prob.apply_H(0, x, th)
+        if V is not None:
+            P.ritz_update("RGen-L(R)", s)
+            Up = U if U is not None else np.zeros((x.size, 0))
+            U, C, Z, mu = orc.refresh(Up, V, AH, lambda v: prob.Jw(0, x, th, v.reshape(x.shape)), s, "rgsv", "L", "R")
+            assert P.recycle_dim(0) == U.shape[1]
+        g = prob.rhs(0, x)
+        w0 = np.zeros_like(g) if w_prev is None else w_prev
+        out = rcg(AH, g, w0, U, C, tol=1e-7 * np.linalg.norm(g), maxit=2000, kmax_store=60)
+        wg = packed([w0.reshape(x.shape)], dt)
+        info = P.hessian_solve(wg, recycle=True, tol=1e-7, relative=True, warm_start=True, maxit=2000)
+        assert abs(info[0]["iters"] - out["iters"]) <= 1, (i, info[0]["iters"], out["iters"])
+        assert rel(wg.cpu().numpy(), out["w"]) < 1e-7
+        V = out["V"]
+        w_prev = out["w"]
+        th = th - 0.05 * rng.standard_normal(th.shape) * 0.1
+
+
+def test_refresh_invariants_fp32():
+    """After bl_ritz_update: C = H U and C^T C = I on the exported recycle space (Section 2.2.2)."""
+    wl = small_wl(sizes=((64, 64), (40, 90)), N=4, seed=7)
+    P, prob, dt = make(wl, "fp32", max_recycle=8, max_basis=60)
+    th = r32(wl.theta0)
+    xs = [r32(x) for x in lower_points(prob, th, gtol=1e-8)]
+    theta = torch.tensor(th, dtype=torch.float64, device=DEV)
+    P.set_point(theta, packed(xs, dt))
+    w = P.zeros()
+    P.hessian_solve(w, recycle=True, tol=1e-5, store_basis=True)
+    for kind in ["Ritz-S", "RGen-L(R)", "HRitz-L"]:
+        P.set_point(theta, packed(xs, dt))
+        w2 = P.zeros()
+        P.hessian_solve(w2, recycle=False, tol=1e-5, store_basis=True)
+        P.ritz_update(kind, 8)
+        for k in range(P.K):
+            s = P.recycle_dim(k)
+            assert s == 8
+            blob = P.recycle_export(k)
+            h, wd = P.sizes[k]
+            n = h * wd
+            arr = np.frombuffer(blob[32:32 + 3 * s * n * 4], dtype=np.float32).astype(np.float64)
+            U = arr[:s * n].reshape(s, n).T
+            Cm = arr[s * n:2 * s * n].reshape(s, n).T
+            np.testing.assert_allclose(Cm.T @ Cm, np.eye(s), atol=2e-4)
+            HU = np.stack([prob.lowers[k].hvp(xs[k], th, U[:, j].reshape(h, wd)).ravel() for j in range(s)], 1)
+            assert np.linalg.norm(HU - Cm) / np.linalg.norm(Cm) < 1e-3, kind
+
+
+def test_lower_solve_first_order_condition():
+    wl = small_wl(sizes=((50, 60), (23, 31)), N=3, seed=9)
+    for precision, gtol in [("fp64", 1e-9), ("fp32", 1e-5)]:
+        P, prob, dt = make(wl, precision)
+        th = r32(wl.theta0) if precision == "fp32" else wl.theta0
+        theta = torch.tensor(th, dtype=torch.float64, device=DEV)
+        x = P.zeros()
+        info = P.lower_solve(theta, x, gtol=gtol, relative=True, max_iters=4000)
+        xs = split(x, P.sizes)
+        for k, ll in enumerate(prob.lowers):
+            g0 = np.linalg.norm(ll.grad(np.zeros_like(xs[k]), th))
+            gn = np.linalg.norm(ll.grad(xs[k], th))
+            assert gn <= 3 * gtol * g0, (precision, k, gn / g0, info[k])
+            assert info[k]["status"] == 0
+
+
+def test_full_hypergradient_fp32():
+    """Lower solve, Hessian solve and J w on the GPU (FP32) against the checker's reference."""
+    wl = small_wl(sizes=((56, 56), (40, 72)), N=4, seed=11)
+    P, prob, dt = make(wl, "fp32", max_recycle=8, max_basis=60)
+    th = r32(wl.theta0)
+    theta = torch.tensor(th, dtype=torch.float64, device=DEV)
+    x = P.zeros()
+    P.lower_solve(theta, x, gtol=1e-6)
+    xs = split(x, P.sizes)
+    w = P.zeros()
+    P.hessian_solve(w, recycle=False, tol=1e-6)
+    mean = P.hypergrad(w).cpu().numpy()
+    refs = [prob.Jw(k, xs[k], th, prob.reference_w(k, xs[k], th)) for k in range(P.K)]
+    assert rel(mean, np.mean(refs, axis=0)) < 1e-4
+
+
+def test_status_codes():
+    wl = small_wl(sizes=((20, 20),), N=2, seed=2)
+    P, prob, dt = make(wl, "fp32", max_recycle=4, max_basis=10)
+    from paper_2412_08264_gb300 import _lib as L
+    w = P.zeros()
+    with pytest.raises(L.BLError) as e:
+        P.hessian_solve(w)                       # no point set yet
+    assert e.value.status == L.BL_ESTATE
+    theta = torch.tensor(r32(wl.theta0), dtype=torch.float64, device=DEV)
+    P.set_point(theta, P.zeros())
+    info = P.hessian_solve(w, recycle=False, tol=1e-12, maxit=1, allow_noconv=True)
+    assert info[0]["status"] == L.BL_ENOCONV and info[0]["iters"] == 1
+    with pytest.raises(L.BLError) as e:
+        P.ritz_update("Ritz-S", 5)               # s above max_recycle
+    assert e.value.status == L.BL_EINVAL
+    with pytest.raises(L.BLError) as e:
+        P.recycle_import(0, b"\x00" * 16)        # truncated checkpoint
+    assert e.value.status == L.BL_EINVAL
+    bad = torch.full((400,), float("nan"), dtype=torch.float32, device=DEV)
+    with pytest.raises(L.BLError) as e:
+        P.hessian_solve(P.zeros(), g=bad, recycle=False, warm_start=False)   # non-finite right-hand side
+    assert e.value.status == L.BL_EBREAKDOWN
