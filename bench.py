@@ -111,6 +111,8 @@ def gpu_arm(args, rank, world, dist):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     wl = synth.batch_64(replica=rank)
+    if args.pairs and args.pairs < len(wl.pairs):
+        wl.pairs, wl.x_star, wl.noise = wl.pairs[:args.pairs], wl.x_star[:args.pairs], wl.noise[:args.pairs]
     K = len(wl.pairs)
     xs_h = torch.tensor(np.concatenate([x.ravel() for x in wl.x_star]), dtype=torch.float32).pin_memory()
     nz_h = torch.tensor(np.concatenate([x.ravel() for x in wl.noise]), dtype=torch.float32).pin_memory()
@@ -122,7 +124,7 @@ def gpu_arm(args, rank, world, dist):
     n_pix = xs.numel()
     strategy = parse(args.strategy)
 
-    def run(strat, steps, warmup, e2e=False, validate=False):
+    def run(strat, steps, warmup, e2e=False, validate=False, profile_range=False):
         P = api.from_workload(wl, y, xs, max_recycle=S_RECYCLE, max_basis=MAX_BASIS)
         y_d = torch.empty_like(y)
         xs_d = torch.empty_like(xs)
@@ -178,12 +180,16 @@ def gpu_arm(args, rank, world, dist):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
+        if profile_range:
+            torch.cuda.profiler.start()
         ev0.record(stream)
         per = None
         for i in range(steps):
             per = step(i, True)
         ev1.record(stream)
         torch.cuda.synchronize()
+        if profile_range:
+            torch.cuda.profiler.stop()
         if world > 1:
             dist.barrier()
         ms = ev0.elapsed_time(ev1)
@@ -205,7 +211,7 @@ def gpu_arm(args, rank, world, dist):
         del P
         return res
 
-    rec = run(strategy, args.steps, args.warmup, validate=True)
+    rec = run(strategy, args.steps, args.warmup, validate=True, profile_range=args.profile_range)
     cg = run(parse("none"), args.steps, args.warmup, validate=True) if (args.compare_cg and strategy.recycles) else None
     e2e = run(strategy, args.steps, args.warmup, e2e=True) if args.e2e else None
     return dict(rec=rec, cg=cg, e2e=e2e, K=K, n_pix=n_pix, wl=wl, strategy=strategy)
@@ -271,6 +277,9 @@ def main():
     ap.add_argument("--no-compare-cg", dest="compare_cg", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--pairs", type=int, default=0, help="use only the first PAIRS pairs (profiling cases)")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (ncu --profile-from-start off)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
