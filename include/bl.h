@@ -240,6 +240,28 @@ bl_status bl_profile_read(bl_problem* prob, int32_t kernel_class, double* total_
 
 const char* bl_last_error(void);
 
+/* J w for one FP32 image without allocating anything (the paper has no counterpart: this is a
+ * service for callers that may not allocate device memory, e.g. code running inside a host
+ * framework that owns the device heap, or under a no-allocation rule after start-up; such callers
+ * cannot create a bl_problem, whose set-up allocates).
+ *   xhat, w:  device, height x width FP32, row-major (the point x^ and the vector w);
+ *   theta:    device, p = n_filters (filter_size^2 + 1) doubles, layout as for bl_problem;
+ *   out:      device, p doubles, receives J w = -(D^2_{theta x} Phi)^T w (the FoE term only,
+ *             as in bl_hypergrad);
+ *   cuda_stream: the stream all work is enqueued on (asynchronous; no synchronisation).
+ * Scratch: a fixed 4 MiB + 32 KiB __device__ array in the library, kept by every GPU that loads
+ * it until the process exits.  Limit: ceil(height / 32) * ceil(width / 32) * p <= 524288, else
+ * BL_EINVAL (e.g. 1024 x 1024 with p <= 511, 512 x 512 with p <= 2048).  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress with that device current);
+ * make that first call before any stream capture.  Every call uses the same array and rewrites
+ * what it reads, so results never depend on an earlier call, but calls whose GPU work overlaps
+ * (unordered streams) race on it: order them on one stream.  No cudaMalloc, cudaFree or
+ * allocating library routine is called.  Returns BL_EINVAL on invalid sizes or options, BL_ECUDA
+ * if a launch fails. */
+bl_status bl_jw_fp32_static(const float* xhat, const float* w, int32_t height, int32_t width,
+                            const double* theta, int32_t n_filters, int32_t filter_size, int32_t phi,
+                            double phi_eps, double* out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,6 +86,8 @@ EXPORTS = {
     "bl_profile_read": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                   C.POINTER(C.c_int64)]),
     "bl_last_error": (C.c_char_p, []),
+    "bl_jw_fp32_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int32,
+                                    C.c_int32, C.c_int32, C.c_double, C.c_void_p, C.c_void_p]),
 }
 
 _lib = None
