@@ -359,7 +359,10 @@ def main():
     if cg is not None:
         ms_cg = tmax(cg["ms"])
         line["plain_cg"] = {"value": K * world * args.steps / (ms_cg / 1e3), "ms_per_step": ms_cg / args.steps,
-                            "krylov_iters_total": int(np.sum(cg["iters"])), "hg_rel_err_max": cg.get("hg_err_max")}
+                            "krylov_iters_total": int(np.sum(cg["iters"])), "hg_rel_err_max": cg.get("hg_err_max"),
+                            "kernel_ms": {k: round(v["ms"], 3) for k, v in cg["prof"].items()},
+                            "hvp_avg_launch_ms": cg["prof"]["hvp"]["ms"] / max(1, cg["prof"]["hvp"]["launches"]),
+                            "hvp_pixels_per_launch": cg["prof"]["hvp"]["pixels"] / max(1, cg["prof"]["hvp"]["launches"])}
     if out["e2e"] is not None:
         ms_e = tmax(out["e2e"]["ms"])
         h2d = 2 * n_pix * 4 + wl.n_params * 8

@@ -69,6 +69,59 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return red[32];
 }
 
+// Per-thread running sums.  GB300 issues FP64 at about 1/64 of the FP32 rate, so FP32 problems
+// accumulate long sums in compensated FP32 (Kahan: the running error term c is fed back into each
+// addition) and switch to FP64 only for the warp / block / tile combine; FP64 problems sum in FP64.
+template <typename T>
+struct Accum;
+template <>
+struct Accum<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+template <>
+struct Accum<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Warp total of per-lane accumulators as a double (valid in every lane): the FP32 variant sums the
+// running sums and the error terms separately in FP32 and combines them in FP64.
+__device__ __forceinline__ double warp_total(const Accum<float>& a) {
+  return (double)warp_sum_f(a.s) - (double)warp_sum_f(a.c);
+}
+__device__ __forceinline__ double warp_total(const Accum<double>& a) { return warp_sum(a.s); }
+
+// Block total of per-thread accumulators (valid in every thread).  red: >= 33 doubles of smem.
+template <int NT, typename A>
+__device__ __forceinline__ double block_total(const A& acc, double* red) {
+  const double v = warp_total(acc);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = (threadIdx.x < NT / 32) ? red[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+    if (threadIdx.x == 0) red[32] = t;
+  }
+  __syncthreads();
+  return red[32];
+}
+
 // Column j of pair `pr` in a batched n x mult matrix (mult = 0: plain batched vector).
 template <typename T>
 __device__ __forceinline__ T* col_ptr(T* base, const PairDev& pr, int mult, int j) {

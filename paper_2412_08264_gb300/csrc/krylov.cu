@@ -38,6 +38,16 @@ struct KrylovArgs {
   int n_tiles, n_chunks;
 };
 
+// Per-chunk partial sums of up to 64 components, one warp total each, written to part[chunk][off + m].
+template <int NT>
+__device__ __forceinline__ void flush_components(const double* warp_vals, int cnt, double* dst) {
+  if ((int)threadIdx.x < cnt) {
+    double t = 0.0;
+    for (int q2 = 0; q2 < NT / 32; ++q2) t += warp_vals[q2 * 65 + threadIdx.x];
+    dst[threadIdx.x] = t;
+  }
+}
+
 // r = g - q (warm) or r = g, w = 0 (cold); partials [0] ||g||^2, [1..s] C^T r.
 template <typename T>
 __global__ void k_init_r(KrylovArgs a, const T* g, const T* q, T* r, T* w, const T* C, int warm,
@@ -50,37 +60,39 @@ __global__ void k_init_r(KrylovArgs a, const T* g, const T* q, T* r, T* w, const
   const int ncomp = 1 + a.SMAX;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const T* Cb = C + pr.off * a.SMAX;
-  for (int cc = 0; cc <= s; cc += 64) {
-    // pass over up to 64 components at a time; component 0 also writes r (and w)
+  {
+    Accum<T> acc;
+    for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
+      const long long gi = pr.off + ch.start + t;
+      const T gv = g[gi];
+      r[gi] = warm ? gv - q[gi] : gv;
+      if (!warm) w[gi] = T(0);
+      acc.add(gv * gv);
+    }
+    const double v = warp_total(acc);
+    if (lane == 0) red[wid * 65] = v;
+  }
+  // each thread reads back only the r values it wrote
+  for (int cc = 1; cc <= s; cc += 64) {
     const int cnt = min(64, s + 1 - cc);
     for (int m = 0; m < cnt; ++m) {
-      const int comp = cc + m;
-      double sum = 0.0;
+      const T* col = Cb + (long long)(cc - 1 + m) * pr.n;
+      Accum<T> acc;
       for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
-        const long long li = ch.start + t, gi = pr.off + li;
-        T rv;
-        if (comp == 0) {
-          const T gv = g[gi];
-          rv = warm ? gv - q[gi] : gv;
-          r[gi] = rv;
-          if (!warm) w[gi] = T(0);
-          sum += (double)gv * (double)gv;
-        } else {
-          rv = r[gi];
-          sum += (double)Cb[(long long)(comp - 1) * pr.n + li] * (double)rv;
-        }
+        const long long li = ch.start + t;
+        acc.add(col[li] * r[pr.off + li]);
       }
-      sum = warp_sum(sum);
-      if (lane == 0) red[wid * 65 + m] = sum;
-      if (comp == 0) __syncthreads();   // r must be written before the C^T r components read it
+      const double v = warp_total(acc);
+      if (lane == 0) red[wid * 65 + 1 + m] = v;
     }
     __syncthreads();
-    if ((int)threadIdx.x < cnt) {
-      double t = 0.0;
-      for (int q2 = 0; q2 < kChunkThreads / 32; ++q2) t += red[q2 * 65 + threadIdx.x];
-      a.cpart[(size_t)blockIdx.x * ncomp + cc + threadIdx.x] = t;
-    }
+    if (cc == 1) flush_components<kChunkThreads>(red, 1 + cnt, a.cpart + (size_t)blockIdx.x * ncomp);
+    else flush_components<kChunkThreads>(red + 1, cnt, a.cpart + (size_t)blockIdx.x * ncomp + cc);
     __syncthreads();
+  }
+  if (s == 0) {
+    __syncthreads();
+    flush_components<kChunkThreads>(red, 1, a.cpart + (size_t)blockIdx.x * ncomp);
   }
 }
 
@@ -103,7 +115,7 @@ __global__ void k_scalar_init1(KrylovArgs a, const int* mask) {
 template <typename T>
 __global__ void k_init2(KrylovArgs a, T* w, T* r, T* p, const T* U, const T* C, const T* Z, const int* mask) {
   __shared__ double red[8 * 65];
-  __shared__ double cs[64];
+  __shared__ T cs[64];
   const ChunkDev ch = a.chunks[blockIdx.x];
   if (!mask[ch.pair]) return;
   const PairDev pr = a.pairs[ch.pair];
@@ -111,54 +123,46 @@ __global__ void k_init2(KrylovArgs a, T* w, T* r, T* p, const T* U, const T* C, 
   const int nz = a.hasz[ch.pair] ? s : 0;
   const int ncomp = 1 + a.SMAX;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if ((int)threadIdx.x < s) cs[threadIdx.x] = a.c[ch.pair * a.SMAX + threadIdx.x];
+  if ((int)threadIdx.x < s) cs[threadIdx.x] = (T)a.c[ch.pair * a.SMAX + threadIdx.x];
   __syncthreads();
   const T* Ub = U + pr.off * a.SMAX;
   const T* Cb = C + pr.off * a.SMAX;
   const T* Zb = Z + pr.off * a.SMAX;
-  double rho = 0.0;
+  Accum<T> rho;
   for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
     const long long li = ch.start + t, gi = pr.off + li;
-    double uc = 0.0, ccv = 0.0;
+    T uc = 0, ccv = 0;
     for (int j = 0; j < s; ++j) {
-      uc += cs[j] * (double)Ub[(long long)j * pr.n + li];
-      ccv += cs[j] * (double)Cb[(long long)j * pr.n + li];
+      uc = fma(cs[j], Ub[(long long)j * pr.n + li], uc);
+      ccv = fma(cs[j], Cb[(long long)j * pr.n + li], ccv);
     }
-    const T wn = w[gi] + (T)uc;
-    const T rn = r[gi] - (T)ccv;
-    w[gi] = wn;
+    const T rn = r[gi] - ccv;
+    w[gi] = w[gi] + uc;
     r[gi] = rn;
     p[gi] = rn;
-    rho += (double)rn * (double)rn;
+    rho.add(rn * rn);
   }
-  rho = warp_sum(rho);
-  if (lane == 0) red[wid * 65] = rho;
-  __syncthreads();
+  {
+    const double v = warp_total(rho);
+    if (lane == 0) red[wid * 65] = v;
+  }
   for (int m = 0; m < nz; ++m) {
-    double sum = 0.0;
+    Accum<T> acc;
     for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
       const long long li = ch.start + t;
-      sum += (double)Zb[(long long)m * pr.n + li] * (double)r[pr.off + li];
+      acc.add(Zb[(long long)m * pr.n + li] * r[pr.off + li]);
     }
-    sum = warp_sum(sum);
-    if (lane == 0) red[wid * 65 + 1 + (m & 63)] = sum;
+    const double v = warp_total(acc);
+    if (lane == 0) red[wid * 65 + 1 + (m & 63)] = v;
     if ((m & 63) == 63 || m == nz - 1) {
       __syncthreads();
       const int base = (m & ~63);
-      const int cnt = m - base + 1;
-      if ((int)threadIdx.x < cnt) {
-        double tt = 0.0;
-        for (int q2 = 0; q2 < kChunkThreads / 32; ++q2) tt += red[q2 * 65 + 1 + threadIdx.x];
-        a.cpart[(size_t)blockIdx.x * ncomp + 1 + base + threadIdx.x] = tt;
-      }
+      flush_components<kChunkThreads>(red + 1, m - base + 1, a.cpart + (size_t)blockIdx.x * ncomp + 1 + base);
       __syncthreads();
     }
   }
-  if (threadIdx.x == 0) {
-    double tt = 0.0;
-    for (int q2 = 0; q2 < kChunkThreads / 32; ++q2) tt += red[q2 * 65];
-    a.cpart[(size_t)blockIdx.x * ncomp] = tt;
-  }
+  __syncthreads();
+  flush_components<kChunkThreads>(red, 1, a.cpart + (size_t)blockIdx.x * ncomp);
 }
 
 // rho, Z^T r, tolerance and the active flags
@@ -228,13 +232,13 @@ __global__ void k_dots(KrylovArgs a, const T* p, const T* q, const T* C, const T
       const int comp = base + m;
       const T* src = comp == 0 ? p + pr.off
                                : (comp <= s ? Cb + (long long)(comp - 1) * pr.n : Zb + (long long)(comp - 1 - s) * pr.n);
-      double sum = 0.0;
+      Accum<T> acc;
       for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
         const long long li = ch.start + t;
-        sum += (double)src[li] * (double)q[pr.off + li];
+        acc.add(src[li] * q[pr.off + li]);
       }
-      sum = warp_sum(sum);
-      if (lane == 0) red[wid * 65 + m] = sum;
+      const double v = warp_total(acc);
+      if (lane == 0) red[wid * 65 + m] = v;
     }
     __syncthreads();
     if ((int)threadIdx.x < cnt) {
@@ -298,32 +302,32 @@ __global__ void k_scalar1(KrylovArgs a, int use_tiles) {
 template <typename T>
 __global__ void k_update(KrylovArgs a, T* w, T* r, const T* p, const T* q, const T* C, T* V, int store) {
   __shared__ double red[40];
-  __shared__ double cs[64];
+  __shared__ T cs[64];
   const ChunkDev ch = a.chunks[blockIdx.x];
   const SolveState S = a.st[ch.pair];
   if (!S.active) return;
   const PairDev pr = a.pairs[ch.pair];
   const int s = a.s_k[ch.pair];
-  if ((int)threadIdx.x < s) cs[threadIdx.x] = a.c[ch.pair * a.SMAX + threadIdx.x];
+  if ((int)threadIdx.x < s) cs[threadIdx.x] = (T)a.c[ch.pair * a.SMAX + threadIdx.x];
   __syncthreads();
   const T* Cb = C + pr.off * a.SMAX;
   T* Vc = store ? V + pr.off * a.KMAX + (long long)(S.iters % a.KMAX) * pr.n : nullptr;
-  const double inv_nr = 1.0 / sqrt(S.rho);
+  const T inv_nr = (T)(1.0 / sqrt(S.rho));
   const T al = (T)S.alpha;
-  double rho = 0.0;
+  Accum<T> rho;
   for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
     const long long li = ch.start + t, gi = pr.off + li;
     const T ro = r[gi];
-    if (store) Vc[li] = (T)((double)ro * inv_nr);
+    if (store) Vc[li] = ro * inv_nr;
     w[gi] = fma(al, p[gi], w[gi]);
-    double ccv = 0.0;
-    for (int j = 0; j < s; ++j) ccv += cs[j] * (double)Cb[(long long)j * pr.n + li];
-    const T rn = ro - al * (q[gi] - (T)ccv);
+    T ccv = 0;
+    for (int j = 0; j < s; ++j) ccv = fma(cs[j], Cb[(long long)j * pr.n + li], ccv);
+    const T rn = ro - al * (q[gi] - ccv);
     r[gi] = rn;
-    rho += (double)rn * (double)rn;
+    rho.add(rn * rn);
   }
-  rho = block_sum<kChunkThreads>(rho, red);
-  if (threadIdx.x == 0) a.cpart[blockIdx.x] = rho;
+  const double tot = block_total<kChunkThreads>(rho, red);
+  if (threadIdx.x == 0) a.cpart[blockIdx.x] = tot;
 }
 
 // rho', beta, stopping test
@@ -383,20 +387,20 @@ __global__ void k_pupdate(KrylovArgs a, const T* r, T* p) {
 // w += U z
 template <typename T>
 __global__ void k_finalize(KrylovArgs a, T* w, const T* U, const int* mask) {
-  __shared__ double zs[64];
+  __shared__ T zs[64];
   const ChunkDev ch = a.chunks[blockIdx.x];
   if (!mask[ch.pair]) return;
   const PairDev pr = a.pairs[ch.pair];
   const int s = a.s_k[ch.pair];
   if (s == 0) return;
-  if ((int)threadIdx.x < s) zs[threadIdx.x] = a.zc[ch.pair * a.SMAX + threadIdx.x];
+  if ((int)threadIdx.x < s) zs[threadIdx.x] = (T)a.zc[ch.pair * a.SMAX + threadIdx.x];
   __syncthreads();
   const T* Ub = U + pr.off * a.SMAX;
   for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
     const long long li = ch.start + t, gi = pr.off + li;
-    double uz = 0.0;
-    for (int j = 0; j < s; ++j) uz += zs[j] * (double)Ub[(long long)j * pr.n + li];
-    w[gi] = w[gi] + (T)uz;
+    T uz = 0;
+    for (int j = 0; j < s; ++j) uz = fma(zs[j], Ub[(long long)j * pr.n + li], uz);
+    w[gi] = w[gi] + uz;
   }
 }
 
@@ -490,6 +494,7 @@ static bl_status solve_impl(bl_problem* P, const int* mask_host, const bl_krylov
     }
     st = launch_hvp(P, p, q, 0, 0, d_itmask, fused ? d_seff : nullptr, fused ? d_hz : nullptr);
     if (st != BL_OK) return st;
+    {
     ProfScope ps(P, BL_KC_KRYLOV);
     if (!fused) {
       k_dots<T><<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a, p, q, C, Z);
@@ -505,8 +510,7 @@ static bl_status solve_impl(bl_problem* P, const int* mask_host, const bl_krylov
     BL_LAUNCH_CHECK(P);
     k_pupdate<T><<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a, r, p);
     BL_LAUNCH_CHECK(P);
-    ps.~ProfScope();
-    ps.slot = -1;
+    }
     BL_CUDA_TRY(cudaMemcpyAsync(P->h_flag, P->d_flag, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
     BL_CUDA_TRY(cudaStreamSynchronize(P->stream));
   }

@@ -21,18 +21,23 @@ struct LbArgs {
   LbfgsState* st;
   int MH;
   double* cpart;    // per chunk, 4 components
-  double* bcoef;    // K x MH: a_i - b_i of the second loop
+  double* acoef;    // K x MH: a_i of the first loop, read by the second
 };
 
 __device__ __forceinline__ int lb_slot(const LbfgsState& S, int i, int MH) {
   return (S.hist_head - 1 - i + 2 * MH) % MH;
 }
 
-// X op= ... : mode 0: X = src (copy); 1: X -= a_i Y_i; 2: X = gamma * X; 3: X += (a_i - b_i) S_i;
-// 4: X = -X.  Then partial dot D^T X with D = dotm[:, slot(idot)] (idot >= 0) or D = dotv.
+// X op= ... : mode 0: X = src (copy); 1: X += coef Y_i; 2: X = gamma * X; 3: X += coef S_i;
+// 5: X = -src.  The coefficient of modes 1 and 3 comes from the partial sums of the previous
+// launch (part_in, one per chunk), which every block reduces over its own pair's chunks in the
+// same order:  mode 1  a_i = rho_i S_i^T q,  coef = -a_i   (a_i kept for the second loop);
+//              mode 3  b_i = rho_i Y_i^T d,  coef = a_i - b_i.
+// Then the partial dot D^T X with D = dotm[:, slot(idot)] (idot >= 0) or D = dotv (idot == -2)
+// goes to part_out (a different buffer from part_in).
 template <typename T>
-__global__ void k_lb_step(LbArgs a, T* X, const T* src, int mode, const T* axm, int iax, const T* dotm, int idot,
-                          const T* dotv) {
+__global__ void k_lb_step(LbArgs a, T* X, const T* src, int mode, const T* axm, int iax, const double* part_in,
+                          const T* dotm, int idot, const T* dotv, double* part_out) {
   __shared__ double red[40];
   const ChunkDev ch = a.chunks[blockIdx.x];
   const LbfgsState S = a.st[ch.pair];
@@ -40,53 +45,50 @@ __global__ void k_lb_step(LbArgs a, T* X, const T* src, int mode, const T* axm, 
   const PairDev pr = a.pairs[ch.pair];
   T coef = 0;
   const T* axc = nullptr;
-  if (mode == 1 && iax < S.hist_count) {
-    coef = (T)(-S.a_hist[iax]);
-    axc = axm + pr.off * a.MH + (long long)lb_slot(S, iax, a.MH) * pr.n;
-  } else if (mode == 3 && iax < S.hist_count) {
-    coef = (T)a.bcoef[ch.pair * a.MH + iax];
+  if ((mode == 1 || mode == 3) && iax < S.hist_count) {
+    double sum = 0.0;
+    for (int u = pr.cbeg; u < pr.cend; ++u) sum += part_in[u];
+    const double v = S.rho_hist[lb_slot(S, iax, a.MH)] * sum;
+    if (mode == 1) {
+      coef = (T)(-v);
+      if (blockIdx.x == pr.cbeg && threadIdx.x == 0) a.acoef[ch.pair * a.MH + iax] = v;
+    } else {
+      coef = (T)(a.acoef[ch.pair * a.MH + iax] - v);
+    }
     axc = axm + pr.off * a.MH + (long long)lb_slot(S, iax, a.MH) * pr.n;
   }
   const T* dc = nullptr;
   if (idot >= 0 && idot < S.hist_count) dc = dotm + pr.off * a.MH + (long long)lb_slot(S, idot, a.MH) * pr.n;
   else if (idot == -2) dc = dotv + pr.off;
   const T gam = (T)S.gamma;
-  double acc = 0.0;
+  Accum<T> acc;
   for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
     const long long li = ch.start + t, gi = pr.off + li;
     T x;
     if (mode == 0) x = src[gi];
     else if (mode == 2) x = gam * X[gi];
-    else if (mode == 4) x = -X[gi];
+    else if (mode == 5) x = -src[gi];
     else {
       x = X[gi];
       if (axc) x = fma(coef, axc[li], x);
     }
     X[gi] = x;
-    if (dc) acc += (double)dc[idot == -2 ? gi - pr.off : li] * (double)x;
+    if (dc) acc.add(dc[li] * x);
   }
-  acc = block_sum<kChunkThreads>(acc, red);
-  if (threadIdx.x == 0) a.cpart[blockIdx.x] = acc;
+  const double tot = block_total<kChunkThreads>(acc, red);
+  if (threadIdx.x == 0) part_out[blockIdx.x] = tot;
 }
 
-// kind 0: a_i = rho_i * sum;  kind 1: b_i = rho_i * sum, bcoef_i = a_i - b_i;
-// kind 2: g^T d = sum (descent check: restart flag if >= 0)
-__global__ void k_lb_coef(LbArgs a, int kind, int i) {
+// g^T d from the partials of the last two-loop launch; descent check (restart flag if >= 0)
+__global__ void k_lb_gtd(LbArgs a, const double* part) {
   const int k = blockIdx.x;
   LbfgsState& S = a.st[k];
   if (!S.active || threadIdx.x != 0) return;
   const PairDev pr = a.pairs[k];
   double sum = 0.0;
-  for (int u = pr.cbeg; u < pr.cend; ++u) sum += a.cpart[u];
-  if (kind == 0) {
-    S.a_hist[i] = (i < S.hist_count) ? S.rho_hist[lb_slot(S, i, a.MH)] * sum : 0.0;
-  } else if (kind == 1) {
-    const double b = (i < S.hist_count) ? S.rho_hist[lb_slot(S, i, a.MH)] * sum : 0.0;
-    a.bcoef[k * a.MH + i] = (i < S.hist_count) ? S.a_hist[i] - b : 0.0;
-  } else {
-    S.gtd = sum;
-    S.accepted = (sum >= 0.0) ? -1 : 0;   // -1: not a descent direction
-  }
+  for (int u = pr.cbeg; u < pr.cend; ++u) sum += part[u];
+  S.gtd = sum;
+  S.accepted = (sum >= 0.0) ? -1 : 0;   // -1: not a descent direction
 }
 
 // d = -g for pairs flagged by the descent check; history cleared
@@ -97,14 +99,14 @@ __global__ void k_lb_restart(LbArgs a, T* d, const T* g) {
   const LbfgsState S = a.st[ch.pair];
   if (!S.active || S.accepted != -1) return;
   const PairDev pr = a.pairs[ch.pair];
-  double acc = 0.0;
+  Accum<T> acc;
   for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
     const long long gi = pr.off + ch.start + t;
     d[gi] = -g[gi];
-    acc -= (double)g[gi] * (double)g[gi];
+    acc.add(-g[gi] * g[gi]);
   }
-  acc = block_sum<kChunkThreads>(acc, red);
-  if (threadIdx.x == 0) a.cpart[blockIdx.x] = acc;
+  const double tot = block_total<kChunkThreads>(acc, red);
+  if (threadIdx.x == 0) a.cpart[blockIdx.x] = tot;
 }
 
 __global__ void k_lb_restart_fix(LbArgs a) {
@@ -173,7 +175,7 @@ __global__ void k_lb_accept(LbArgs a, T* x, T* g, const T* xt, const T* gt, T* S
   const PairDev pr = a.pairs[ch.pair];
   T* sc = Sm + pr.off * a.MH + (long long)S.hist_head * pr.n;
   T* yc = Ym + pr.off * a.MH + (long long)S.hist_head * pr.n;
-  double sy = 0, yy = 0, ss = 0, gg = 0;
+  Accum<T> sy, yy, ss, gg;
   for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
     const long long li = ch.start + t, gi = pr.off + li;
     const T xn = xt[gi], gn = gt[gi];
@@ -182,20 +184,20 @@ __global__ void k_lb_accept(LbArgs a, T* x, T* g, const T* xt, const T* gt, T* S
     yc[li] = yv;
     x[gi] = xn;
     g[gi] = gn;
-    sy += (double)sv * (double)yv;
-    yy += (double)yv * (double)yv;
-    ss += (double)sv * (double)sv;
-    gg += (double)gn * (double)gn;
+    sy.add(sv * yv);
+    yy.add(yv * yv);
+    ss.add(sv * sv);
+    gg.add(gn * gn);
   }
-  sy = block_sum<kChunkThreads>(sy, red);
-  yy = block_sum<kChunkThreads>(yy, red);
-  ss = block_sum<kChunkThreads>(ss, red);
-  gg = block_sum<kChunkThreads>(gg, red);
+  const double t0 = block_total<kChunkThreads>(sy, red);
+  const double t1 = block_total<kChunkThreads>(yy, red);
+  const double t2 = block_total<kChunkThreads>(ss, red);
+  const double t3 = block_total<kChunkThreads>(gg, red);
   if (threadIdx.x == 0) {
-    a.cpart[(size_t)blockIdx.x * 4 + 0] = sy;
-    a.cpart[(size_t)blockIdx.x * 4 + 1] = yy;
-    a.cpart[(size_t)blockIdx.x * 4 + 2] = ss;
-    a.cpart[(size_t)blockIdx.x * 4 + 3] = gg;
+    a.cpart[(size_t)blockIdx.x * 4 + 0] = t0;
+    a.cpart[(size_t)blockIdx.x * 4 + 1] = t1;
+    a.cpart[(size_t)blockIdx.x * 4 + 2] = t2;
+    a.cpart[(size_t)blockIdx.x * 4 + 3] = t3;
   }
 }
 
@@ -271,7 +273,7 @@ static bl_status lbfgs_impl(bl_problem* P, const std::vector<int>& mask_host, co
   a.st = P->lst;
   a.MH = MH;
   a.cpart = P->cpart;
-  a.bcoef = P->dY3;   // K x MH doubles of scratch
+  a.acoef = P->dY3;   // K x MH doubles of scratch
   const int* mask = P->d_active;
   int* smask = P->d_active + K;
   T* x = (T*)P->lx;
@@ -310,29 +312,32 @@ static bl_status lbfgs_impl(bl_problem* P, const std::vector<int>& mask_host, co
     const int m = std::min(hist, MH);
     {
     ProfScope ps(P, BL_KC_LBFGS);
-    k_lb_step<T><<<cg, ct, 0, P->stream>>>(a, q, g, 0, nullptr, 0, Sm, m > 0 ? 0 : -1, nullptr);
+    double* pb[2] = {P->cpart, P->cpart + P->n_chunks};   // ping-pong partial sums
+    int cur = 0;
+    k_lb_step<T><<<cg, ct, 0, P->stream>>>(a, q, g, 0, nullptr, 0, nullptr, Sm, m > 0 ? 0 : -1, nullptr, pb[cur]);
     BL_LAUNCH_CHECK(P);
     for (int i = 0; i < m; ++i) {
-      k_lb_coef<<<K, 32, 0, P->stream>>>(a, 0, i);
+      k_lb_step<T><<<cg, ct, 0, P->stream>>>(a, q, nullptr, 1, Ym, i, pb[cur], Sm, i + 1 < m ? i + 1 : -1,
+                                             nullptr, pb[cur ^ 1]);
       BL_LAUNCH_CHECK(P);
-      k_lb_step<T><<<cg, ct, 0, P->stream>>>(a, q, nullptr, 1, Ym, i, Sm, i + 1 < m ? i + 1 : -1, nullptr);
-      BL_LAUNCH_CHECK(P);
+      cur ^= 1;
     }
-    // d = gamma q; oldest to newest
-    k_lb_step<T><<<cg, ct, 0, P->stream>>>(a, q, nullptr, 2, nullptr, 0, Ym, m > 0 ? m - 1 : -1, nullptr);
+    // q = gamma q; oldest to newest
+    k_lb_step<T><<<cg, ct, 0, P->stream>>>(a, q, nullptr, 2, nullptr, 0, nullptr, Ym, m > 0 ? m - 1 : -1, nullptr,
+                                           pb[cur ^ 1]);
     BL_LAUNCH_CHECK(P);
+    cur ^= 1;
     for (int i = m - 1; i >= 0; --i) {
-      k_lb_coef<<<K, 32, 0, P->stream>>>(a, 1, i);
+      k_lb_step<T><<<cg, ct, 0, P->stream>>>(a, q, nullptr, 3, Sm, i, pb[cur], Ym, i > 0 ? i - 1 : -1, nullptr,
+                                             pb[cur ^ 1]);
       BL_LAUNCH_CHECK(P);
-      k_lb_step<T><<<cg, ct, 0, P->stream>>>(a, q, nullptr, 3, Sm, i, Ym, i > 0 ? i - 1 : -1, nullptr);
-      BL_LAUNCH_CHECK(P);
+      cur ^= 1;
     }
     // d = -q with g^T d
-    k_lb_step<T><<<cg, ct, 0, P->stream>>>(a, d, q, 0, nullptr, 0, nullptr, -1, nullptr);
+    k_lb_step<T><<<cg, ct, 0, P->stream>>>(a, d, q, 5, nullptr, 0, nullptr, nullptr, -2, g, pb[cur ^ 1]);
     BL_LAUNCH_CHECK(P);
-    k_lb_step<T><<<cg, ct, 0, P->stream>>>(a, d, nullptr, 4, nullptr, 0, nullptr, -2, g);
-    BL_LAUNCH_CHECK(P);
-    k_lb_coef<<<K, 32, 0, P->stream>>>(a, 2, 0);
+    cur ^= 1;
+    k_lb_gtd<<<K, 32, 0, P->stream>>>(a, pb[cur]);
     BL_LAUNCH_CHECK(P);
     k_lb_restart<T><<<cg, ct, 0, P->stream>>>(a, d, g);
     BL_LAUNCH_CHECK(P);

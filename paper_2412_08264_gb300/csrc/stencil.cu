@@ -17,14 +17,29 @@
 namespace bl {
 
 // acc[yy][xx] += sum_{a,b} tap(a, b) src[(yy + a) * ld + xx + b]; tap = k[a][b] or k flipped.
-template <int F, int BY, int BX, bool FLIP, typename T>
+// ALIGNED: the caller guarantees src and ld are 16-byte multiples, so FP32 row windows whose
+// length is a multiple of 4 are read with 128-bit shared loads.
+template <int F, int BY, int BX, bool FLIP, bool ALIGNED = false, typename T>
 __device__ __forceinline__ void corr_block(const T* __restrict__ src, int ld, const T (&k)[F * F],
                                            T (&acc)[BY][BX]) {
+  constexpr int NS = BX + F - 1;
+  constexpr bool kVec = ALIGNED && sizeof(T) == 4 && NS % 4 == 0;
 #pragma unroll
   for (int ry = 0; ry < BY + F - 1; ++ry) {
-    T seg[BX + F - 1];
+    T seg[NS];
+    if constexpr (kVec) {
 #pragma unroll
-    for (int c = 0; c < BX + F - 1; ++c) seg[c] = src[ry * ld + c];
+      for (int c = 0; c < NS; c += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(&src[ry * ld + c]);
+        seg[c] = v.x;
+        seg[c + 1] = v.y;
+        seg[c + 2] = v.z;
+        seg[c + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < NS; ++c) seg[c] = src[ry * ld + c];
+    }
 #pragma unroll
     for (int yy = 0; yy < BY; ++yy) {
       const int a = ry - yy;
@@ -38,6 +53,18 @@ __device__ __forceinline__ void corr_block(const T* __restrict__ src, int ld, co
     }
   }
 }
+
+// Asynchronous global -> shared copies of single elements (cp.async, L1-allocating).
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 template <typename T>
 struct StencilArgs {
@@ -79,7 +106,7 @@ struct StencilSmem {
   static constexpr int ZP = kTileRegion + 4;        // pitch of the z buffer
   static constexpr int E2MAX = TILE + 2 * BL_MAX_BLUR_RADIUS;
   static constexpr size_t vs = (size_t)VD * VD;
-  static constexpr size_t zs = (size_t)kTileRegion * ZP;
+  static constexpr size_t zs = 2 * (size_t)kTileRegion * ZP;   // double-buffered z_j
   static constexpr size_t h1 = (size_t)VD * VD;
   static constexpr size_t av = (size_t)E2MAX * E2MAX;
   __host__ __device__ static size_t taps(int N) { return ((size_t)N * F * F + 1) & ~(size_t)1; }   // keeps red 8-byte aligned
@@ -89,7 +116,7 @@ struct StencilSmem {
 };
 
 template <typename T, int F, int MODE>
-__global__ void __launch_bounds__(kStencilThreads, 1) k_foe_stencil(StencilArgs<T> a) {
+__global__ void __launch_bounds__(kStencilThreads, sizeof(T) == 4 ? 2 : 1) k_foe_stencil(StencilArgs<T> a) {
   using S = StencilSmem<T, F>;
   constexpr int R = S::R, TILE = S::TILE, VD = S::VD, ZP = S::ZP;
   constexpr int NB = TILE / 4;                       // owner blocks per side
@@ -140,7 +167,7 @@ __global__ void __launch_bounds__(kStencilThreads, 1) k_foe_stencil(StencilArgs<
     h1[y * VD + x] = s;
   }
   __syncthreads();
-  double dterm = 0.0;                                  // GRAD: ||A x - y||^2 over the tile
+  Accum<T> dterm;                                       // GRAD: ||A x - y||^2 over the tile
   // av[i][x] = sum_a g[a] h1[i + a + sh][x], masked to the image (and minus y in GRAD mode)
   for (int idx = tid; idx < E2 * E2; idx += kStencilThreads) {
     const int i = idx / E2, x = idx - (idx / E2) * E2;
@@ -152,7 +179,7 @@ __global__ void __launch_bounds__(kStencilThreads, 1) k_foe_stencil(StencilArgs<
     const bool inside = iy >= 0 && iy < h && ix >= 0 && ix < w;
     if (MODE == kModeGrad && inside) {
       s -= a.y[pr.off + (long long)iy * w + ix];
-      if (i >= rb && i < rb + TILE && x >= rb && x < rb + TILE) dterm += (double)s * (double)s;
+      if (i >= rb && i < rb + TILE && x >= rb && x < rb + TILE) dterm.add(s * s);
     }
     av[i * S::E2MAX + x] = inside ? s : T(0);
   }
@@ -185,8 +212,36 @@ __global__ void __launch_bounds__(kStencilThreads, 1) k_foe_stencil(StencilArgs<
   // ---- regulariser part: per filter z_j on the tile grown by R, then K_j^T z_j ----
   const int sby = tid >> 4, sbx = tid & 15;             // step-1 block of this thread
   constexpr int E1 = TILE + 2 * R;
-  double rterm = 0.0;                                   // GRAD: sum e^alpha phi(u) over the tile
+  constexpr bool kAligned = (kHalo - 2 * R) % 4 == 0 && VD % 4 == 0 && ZP % 4 == 0;
+  Accum<T> rterm;                                       // GRAD: sum e^alpha phi(u) over the tile
+  // HVP: the 16 field values d_j of this thread's step-1 block are prefetched one filter ahead
+  // with cp.async into a per-thread slot of a double buffer that reuses the (now dead) blur
+  // buffers; element e of thread t sits at e * 256 + t, so the reads are conflict-free.
+  T* dbuf = h1;
+  // 4x4 blocks wholly outside the image (ragged tiles) or beyond the region skip their arithmetic
+  const bool s1_live = 4 * sby < E1 && 4 * sbx < E1 && oy - R + 4 * sby < h && ox - R + 4 * sbx < w &&
+                       oy - R + 4 * sby + 3 >= 0 && ox - R + 4 * sbx + 3 >= 0;
+  const bool s2_live = owner && oy + 4 * oby < h && ox + 4 * obx < w;
+  __syncthreads();                                      // every thread is done with h1 / av
+  auto prefetch = [&](int jf, int buf) {
+#pragma unroll
+    for (int yy = 0; yy < 4; ++yy)
+#pragma unroll
+      for (int xx = 0; xx < 4; ++xx) {
+        const int ey = 4 * sby + yy, ex = 4 * sbx + xx;
+        const int iy = oy - R + ey, ix = ox - R + ex;
+        T* dst = &dbuf[(buf * 16 + yy * 4 + xx) * kStencilThreads + tid];
+        if (ey < E1 && ex < E1 && iy >= 0 && iy < h && ix >= 0 && ix < w)
+          cp_async_elem(dst, &a.fd[(long long)jf * a.n_tot + pr.off + (long long)iy * w + ix]);
+        else
+          *dst = T(0);
+      }
+  };
+  if (MODE == kModeHvp && a.N > 0) prefetch(0, 0);
+  cp_async_commit();
   for (int jf = 0; jf < a.N; ++jf) {
+    if (MODE == kModeHvp && jf + 1 < a.N) prefetch(jf + 1, (jf + 1) & 1);
+    cp_async_commit();
     T k[F * F];
 #pragma unroll
     for (int t = 0; t < F * F; ++t) k[t] = tps[jf * F * F + t];
@@ -196,32 +251,35 @@ __global__ void __launch_bounds__(kStencilThreads, 1) k_foe_stencil(StencilArgs<
     for (int yy = 0; yy < 4; ++yy)
 #pragma unroll
       for (int xx = 0; xx < 4; ++xx) u[yy][xx] = 0;
-    corr_block<F, 4, 4, false>(&vs[(4 * sby + kHalo - 2 * R) * VD + 4 * sbx + kHalo - 2 * R], VD, k, u);
+    if (s1_live)
+      corr_block<F, 4, 4, false, kAligned>(&vs[(4 * sby + kHalo - 2 * R) * VD + 4 * sbx + kHalo - 2 * R], VD, k, u);
+    T* zb = zs + (jf & 1) * (kTileRegion * ZP);
+    if (MODE == kModeHvp) cp_async_wait_prev();       // this thread's d_j values have landed
 #pragma unroll
     for (int yy = 0; yy < 4; ++yy)
 #pragma unroll
       for (int xx = 0; xx < 4; ++xx) {
         const int ey = 4 * sby + yy, ex = 4 * sbx + xx;
-        const int iy = oy - R + ey, ix = ox - R + ex;
-        const bool inside = ey < E1 && ex < E1 && iy >= 0 && iy < h && ix >= 0 && ix < w;
         T z = 0;
-        if (inside) {
-          const long long pix = pr.off + (long long)iy * w + ix;
-          if (MODE == kModeHvp) {
-            z = a.fd[(long long)jf * a.n_tot + pix] * u[yy][xx];
-          } else {
+        if (MODE == kModeHvp) {
+          z = dbuf[((jf & 1) * 16 + yy * 4 + xx) * kStencilThreads + tid] * u[yy][xx];
+        } else {
+          const int iy = oy - R + ey, ix = ox - R + ex;
+          if (ey < E1 && ex < E1 && iy >= 0 && iy < h && ix >= 0 && ix < w) {
             T f0, d1, d2;
             phi_all(u[yy][xx], a.eps, a.phi, f0, d1, d2);
             z = ea * d1;
-            if (ey >= R && ey < R + TILE && ex >= R && ex < R + TILE) rterm += (double)ea * (double)f0;
+            if (ey >= R && ey < R + TILE && ex >= R && ex < R + TILE) rterm.add(ea * f0);
           }
         }
-        zs[ey * ZP + ex] = z;
+        zb[ey * ZP + ex] = z;
       }
+    // one barrier per filter: z is double-buffered, so the buffer written next iteration was last
+    // read before this barrier
     __syncthreads();
-    if (owner) corr_block<F, 4, 4, true>(&zs[(4 * oby) * ZP + 4 * obx], ZP, k, outacc);
-    __syncthreads();
+    if (s2_live) corr_block<F, 4, 4, true, kAligned>(&zb[(4 * oby) * ZP + 4 * obx], ZP, k, outacc);
   }
+  __syncthreads();
 
   // ---- write the owned block ----
   T* out = col_ptr(a.out, pr, a.mult, col);
@@ -238,20 +296,20 @@ __global__ void __launch_bounds__(kStencilThreads, 1) k_foe_stencil(StencilArgs<
 
   if (MODE == kModeGrad) {
     // value partials of this tile: ||A x - y||^2, sum e^alpha phi, ||x||^2 (owned pixels)
-    double xx2 = 0.0;
+    Accum<T> xx2;
     if (owner) {
       for (int yy = 0; yy < 4; ++yy)
         for (int xx = 0; xx < 4; ++xx) {
           const int iy = oy + 4 * oby + yy, ix = ox + 4 * obx + xx;
           if (4 * oby + yy < TILE && 4 * obx + xx < TILE && iy < h && ix < w) {
-            const double v = (double)vs[(4 * oby + yy + kHalo) * VD + 4 * obx + xx + kHalo];
-            xx2 += v * v;
+            const T v = vs[(4 * oby + yy + kHalo) * VD + 4 * obx + xx + kHalo];
+            xx2.add(v * v);
           }
         }
     }
-    const double t0 = block_sum<kStencilThreads>(dterm, red);
-    const double t1 = block_sum<kStencilThreads>(rterm, red);
-    const double t2 = block_sum<kStencilThreads>(xx2, red);
+    const double t0 = block_total<kStencilThreads>(dterm, red);
+    const double t1 = block_total<kStencilThreads>(rterm, red);
+    const double t2 = block_total<kStencilThreads>(xx2, red);
     if (tid == 0) {
       a.tpart[(size_t)blockIdx.x * 3 + 0] = t0;
       a.tpart[(size_t)blockIdx.x * 3 + 1] = t1;
@@ -260,45 +318,40 @@ __global__ void __launch_bounds__(kStencilThreads, 1) k_foe_stencil(StencilArgs<
   }
 
   if (MODE == kModeHvp && a.dots) {
-    // tile partials: [0] p^T q, [1 .. s] C^T q, [1 + SMAX .. 1 + SMAX + s) Z^T q
+    // tile partials: [0] p^T q, [1 .. s] C^T q, [1 + SMAX .. 1 + SMAX + s) Z^T q.  q is staged in the
+    // (now free) z buffer; each warp then streams whole columns of C or Z over the tile's rows
+    // (coalesced), summing in compensated FP32 per lane and in FP64 across lanes.
     const int s = a.s_k[tl.pair];
     const int nz = a.hasz[tl.pair] ? s : 0;
     const int lane = tid & 31, wid = tid >> 5;
+    const int vh = min(TILE, h - oy), vw = min(TILE, w - ox);
+    T* qs = zs;
+    if (owner) {
+#pragma unroll
+      for (int yy = 0; yy < 4; ++yy)
+#pragma unroll
+        for (int xx = 0; xx < 4; ++xx)
+          if (4 * oby + yy < vh && 4 * obx + xx < vw) qs[(4 * oby + yy) * TILE + 4 * obx + xx] = outacc[yy][xx];
+    }
+    __syncthreads();
     const T* Cb = a.C + pr.off * a.SMAX;
     const T* Zb = a.Z + pr.off * a.SMAX;
-    const int ncomp = a.ncomp;
-    for (int cc = 0; cc < 1 + s + nz; ++cc) {
-      double acc = 0.0;
-      if (owner) {
-        const T* src = nullptr;
-        if (cc >= 1 && cc <= s) src = Cb + (long long)(cc - 1) * pr.n;
-        else if (cc > s) src = Zb + (long long)(cc - 1 - s) * pr.n;
-        for (int yy = 0; yy < 4; ++yy) {
-          const int iy = oy + 4 * oby + yy;
-          if (4 * oby + yy >= TILE || iy >= h) continue;
-          for (int xx = 0; xx < 4; ++xx) {
-            const int ix = ox + 4 * obx + xx;
-            if (4 * obx + xx >= TILE || ix >= w) continue;
-            const T other = (cc == 0) ? vs[(4 * oby + yy + kHalo) * VD + 4 * obx + xx + kHalo]
-                                      : src[(long long)iy * w + ix];
-            acc += (double)(other * outacc[yy][xx]);
-          }
+    for (int cc = wid; cc < 1 + s + nz; cc += kStencilThreads / 32) {
+      Accum<T> acc;
+      if (cc == 0) {
+        for (int i = 0; i < vh; ++i)
+          for (int j = lane; j < vw; j += 32) acc.add(vs[(i + kHalo) * VD + j + kHalo] * qs[i * TILE + j]);
+      } else {
+        const T* col = cc <= s ? Cb + (long long)(cc - 1) * pr.n : Zb + (long long)(cc - 1 - s) * pr.n;
+        for (int i = 0; i < vh; ++i) {
+          const T* row = col + (long long)(oy + i) * w + ox;
+          for (int j = lane; j < vw; j += 32) acc.add(row[j] * qs[i * TILE + j]);
         }
       }
-      acc = warp_sum(acc);
-      if (lane == 0) red[wid * 64 + (cc & 63)] = acc;
-      if ((cc & 63) == 63 || cc == s + nz) {
-        __syncthreads();
-        const int base = cc & ~63;
-        const int cnt = cc - base + 1;
-        if (tid < cnt) {
-          double t = 0.0;
-          for (int q = 0; q < kStencilThreads / 32; ++q) t += red[q * 64 + tid];
-          const int comp = base + tid;
-          const int slot = comp <= s ? comp : comp - s + a.SMAX;   // Z^T q after SMAX C slots
-          a.tpart[(size_t)blockIdx.x * ncomp + slot] = t;
-        }
-        __syncthreads();
+      const double v = warp_total(acc);
+      if (lane == 0) {
+        const int slot = cc <= s ? cc : cc - s + a.SMAX;   // Z^T q after SMAX C slots
+        a.tpart[(size_t)blockIdx.x * a.ncomp + slot] = v;
       }
     }
   }
@@ -343,7 +396,7 @@ __global__ void k_fields(const PairDev* pairs, const ChunkDev* chunks, const T* 
 //   (J w)_{k_j[o]}   = -e^{alpha_j} sum_p [ e_p w_{p+o} + phi''(u_p) (k_j * w)_p x^_{p+o} ]
 // Tile partials: tpart[((col * n_tiles) + tile) * p + m].
 template <typename T, int F>
-__global__ void __launch_bounds__(kStencilThreads, 1)
+__global__ void __launch_bounds__(kStencilThreads, sizeof(T) == 4 ? 2 : 1)
 k_foe_jw(const PairDev* pairs, const TileDev* tiles, int n_tiles, const T* win, int mult,
          const int* cols, const T* xhat, const T* fu, const T* taps, const double* ealpha, int N,
          T eps, int phi, long long n_tot, const int* mask, double* tpart, int p, unsigned long long* pix) {
@@ -359,9 +412,11 @@ k_foe_jw(const PairDev* pairs, const TileDev* tiles, int n_tiles, const T* win, 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ws = reinterpret_cast<T*>(smem_raw);
   T* xs = ws + RS * RS;
-  double* red = reinterpret_cast<double*>(xs + RS * RS);              // 8 x (FF + 1)
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  T* fbuf = xs + RS * RS;                                             // 2 x 16 x 256 prefetched u_j
+  T* rf = fbuf + 2 * 16 * kStencilThreads;                            // (FF + 1) x 256 per-thread sums
+  const int tid = threadIdx.x, lane = tid & 31;
   const T* wv = col_ptr(win, pr, mult, col);
+  constexpr bool kAligned = RS % 4 == 0;
   for (int idx = tid; idx < RS * RS; idx += kStencilThreads) {
     const int i = idx / RS, j = idx - (idx / RS) * RS;
     const int iy = tl.oy - R + i, ix = tl.ox - R + j;
@@ -373,7 +428,25 @@ k_foe_jw(const PairDev* pairs, const TileDev* tiles, int n_tiles, const T* win, 
   const bool owner = tid < NB * NB;
   const int oby = owner ? tid / NB : 0, obx = owner ? tid - (tid / NB) * NB : 0;
   double* outp = tpart + ((size_t)col * n_tiles + blockIdx.x) * p;
+  // u_j of this thread's 16 pixels is prefetched one filter ahead (cp.async, per-thread slots)
+  auto prefetch = [&](int jf, int buf) {
+#pragma unroll
+    for (int yy = 0; yy < 4; ++yy)
+#pragma unroll
+      for (int xx = 0; xx < 4; ++xx) {
+        const int iy = tl.oy + 4 * oby + yy, ix = tl.ox + 4 * obx + xx;
+        T* dst = &fbuf[(buf * 16 + yy * 4 + xx) * kStencilThreads + tid];
+        if (owner && 4 * oby + yy < TILE && 4 * obx + xx < TILE && iy < pr.h && ix < pr.w)
+          cp_async_elem(dst, &fu[(long long)jf * n_tot + pr.off + (long long)iy * pr.w + ix]);
+        else
+          *dst = T(0);
+      }
+  };
+  if (N > 0) prefetch(0, 0);
+  cp_async_commit();
   for (int jf = 0; jf < N; ++jf) {
+    if (jf + 1 < N) prefetch(jf + 1, (jf + 1) & 1);
+    cp_async_commit();
     T k[FF];
 #pragma unroll
     for (int t = 0; t < FF; ++t) k[t] = taps[jf * FF + t];
@@ -382,8 +455,9 @@ k_foe_jw(const PairDev* pairs, const TileDev* tiles, int n_tiles, const T* win, 
     for (int yy = 0; yy < 4; ++yy)
 #pragma unroll
       for (int xx = 0; xx < 4; ++xx) kw[yy][xx] = 0;
-    corr_block<F, 4, 4, false>(&ws[(4 * oby) * RS + 4 * obx], RS, k, kw);
-    double ga = 0.0;
+    corr_block<F, 4, 4, false, kAligned>(&ws[(4 * oby) * RS + 4 * obx], RS, k, kw);
+    cp_async_wait_prev();
+    T ga = 0;
 #pragma unroll
     for (int yy = 0; yy < 4; ++yy)
 #pragma unroll
@@ -392,10 +466,10 @@ k_foe_jw(const PairDev* pairs, const TileDev* tiles, int n_tiles, const T* win, 
         const bool in = owner && 4 * oby + yy < TILE && 4 * obx + xx < TILE && iy < pr.h && ix < pr.w;
         T ee = 0, dd = 0;
         if (in) {
-          const T uu = fu[(long long)jf * n_tot + pr.off + (long long)iy * pr.w + ix];
+          const T uu = fbuf[((jf & 1) * 16 + yy * 4 + xx) * kStencilThreads + tid];
           ee = phi_d1(uu, eps, phi);
           dd = phi_d2(uu, eps, phi) * kw[yy][xx];
-          ga += (double)(ee * kw[yy][xx]);
+          ga = fma(ee, kw[yy][xx], ga);
         }
         e[yy][xx] = ee;
         d[yy][xx] = dd;
@@ -422,20 +496,27 @@ k_foe_jw(const PairDev* pairs, const TileDev* tiles, int n_tiles, const T* win, 
             gt[aa * F + b] = fma(e[yy][xx], wseg[xx + b], fma(d[yy][xx], xseg[xx + b], gt[aa * F + b]));
       }
     }
-    // block reduction of FF + 1 values
-    const double scale = -ealpha[jf];
-    double v = warp_sum(ga);
-    if (lane == 0) red[wid * (FF + 1)] = v;
+    // Block reduction of the FF + 1 sums: every thread parks its values in smem (value-major,
+    // rf[v * 256 + thread]); then lane l of warp w sums value v = 4 w + l / 8 over the 32 threads
+    // of segment l % 8 (rotated by the lane, so the 8 segments hit distinct banks) in compensated
+    // FP32, and the 8 segment totals of a value combine in FP64 through 3 shuffles.
+    rf[tid] = ga;
 #pragma unroll
-    for (int t = 0; t < FF; ++t) {
-      double q = warp_sum((double)gt[t]);
-      if (lane == 0) red[wid * (FF + 1) + 1 + t] = q;
-    }
+    for (int t = 0; t < FF; ++t) rf[(1 + t) * kStencilThreads + tid] = gt[t];
     __syncthreads();
-    if (tid < FF + 1) {
-      double s = 0.0;
-      for (int q = 0; q < kStencilThreads / 32; ++q) s += red[q * (FF + 1) + tid];
-      outp[jf * (FF + 1) + tid] = scale * s;
+    const double scale = -ealpha[jf];
+    for (int job = tid; job < 8 * ((FF + 1 + 3) / 4) * 4; job += kStencilThreads) {
+      const int v = job >> 3, seg = job & 7;
+      Accum<T> acc;
+      if (v < FF + 1) {
+#pragma unroll 8
+        for (int i = 0; i < 32; ++i) acc.add(rf[v * kStencilThreads + seg * 32 + ((i + lane) & 31)]);
+      }
+      double tot = acc.value();
+      tot += __shfl_xor_sync(0xffffffffu, tot, 1);
+      tot += __shfl_xor_sync(0xffffffffu, tot, 2);
+      tot += __shfl_xor_sync(0xffffffffu, tot, 4);
+      if (seg == 0 && v < FF + 1) outp[jf * (FF + 1) + v] = scale * tot;
     }
     __syncthreads();
   }
@@ -841,7 +922,8 @@ static bl_status jw_impl(bl_problem* P, const void* in, int mult, int cols, cons
 #define BL_JW_CASE(FF)                                                                            \
   case FF: {                                                                                      \
     constexpr int RS = tile_out(FF) + 2 * (FF / 2);                                               \
-    size_t sm = 2 * (size_t)RS * RS * sizeof(T) + 8 * (FF * FF + 1) * sizeof(double);             \
+    size_t sm = (2 * (size_t)RS * RS + 2 * 16 * kStencilThreads +                                 \
+                 (size_t)(FF * FF + 1) * kStencilThreads) * sizeof(T);                            \
     BL_CUDA_TRY(cudaFuncSetAttribute(k_foe_jw<T, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                      (int)sm));                                                   \
     k_foe_jw<T, FF><<<grid, kStencilThreads, sm, P->stream>>>(                                    \

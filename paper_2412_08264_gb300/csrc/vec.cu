@@ -151,12 +151,12 @@ __global__ void k_dot(const PairDev* pairs, const ChunkDev* chunks, const T* a, 
   const ChunkDev ch = chunks[blockIdx.x];
   if (mask && !mask[ch.pair]) return;
   const PairDev pr = pairs[ch.pair];
-  double s = 0.0;
+  Accum<T> acc;
   for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
     const long long i = pr.off + ch.start + t;
-    s += (double)a[i] * (double)b[i];
+    acc.add(a[i] * b[i]);
   }
-  s = block_sum<kChunkThreads>(s, red);
+  const double s = block_total<kChunkThreads>(acc, red);
   if (threadIdx.x == 0) cpart[blockIdx.x] = s;
 }
 
