@@ -106,6 +106,7 @@ class Clocks:
 def gpu_arm(args, rank, world, dist):
     import torch
     from paper_2412_08264_gb300 import api, synth
+    from paper_2412_08264_gb300.parallel import allreduce_mean
     from paper_2412_08264_gb300.strategy import parse
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
@@ -124,7 +125,7 @@ def gpu_arm(args, rank, world, dist):
     n_pix = xs.numel()
     strategy = parse(args.strategy)
 
-    def run(strat, steps, warmup, e2e=False, validate=False, profile_range=False):
+    def run(strat, steps, warmup, e2e=False, validate=False, profile_range=False, prof_steps=0):
         P = api.from_workload(wl, y, xs, max_recycle=S_RECYCLE, max_basis=MAX_BASIS)
         y_d = torch.empty_like(y)
         xs_d = torch.empty_like(xs)
@@ -153,8 +154,7 @@ def gpu_arm(args, rank, world, dist):
                                    nsc_scale=None if hg_prev is None else [hg_prev] * K, allow_noconv=True)
             mean, per = P.hypergrad(w, per_pair=True)
             if world > 1:
-                dist.all_reduce(mean)
-                mean /= world
+                mean = allreduce_mean(mean, K)
             g = mean.cpu().numpy()                       # the step's result, read back every step
             hg_prev = float(np.linalg.norm(g))
             # Adam (Section 5.2: fixed step length 1e-2)
@@ -175,7 +175,6 @@ def gpu_arm(args, rank, world, dist):
             dist.barrier()
         clocks = Clocks(dev.index)
         clocks.start()
-        P.profile(True)
         launches0 = P.launch_count()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
@@ -193,11 +192,10 @@ def gpu_arm(args, rank, world, dist):
         if world > 1:
             dist.barrier()
         ms = ev0.elapsed_time(ev1)
-        prof = P.profile_read()
-        P.profile(False)
         launches = P.launch_count() - launches0
+        graph_used = P.graph_used()
         ck = clocks.stop()
-        res = dict(ms=ms, iters=iters, prof=prof, launches=launches, clocks=ck)
+        val = {}
         if validate:
             # tight reference at the last step's point: plain CG to rtol 1e-7 from the computed w
             wref = w.clone()
@@ -206,13 +204,30 @@ def gpu_arm(args, rank, world, dist):
             _, per_ref = P.hypergrad(wref, per_pair=True)
             err = (per - per_ref).norm(dim=1) / per_ref.norm(dim=1)
             mean_err = float((per.mean(0) - per_ref.mean(0)).norm() / per_ref.mean(0).norm())
-            res["hg_err_max"] = float(err.max())
-            res["hg_err_mean_grad"] = mean_err
+            val["hg_err_max"] = float(err.max())
+            val["hg_err_mean_grad"] = mean_err
+        # per-kernel CUDA-event timing over further steps of the same sequence (profiling makes the
+        # library launch the Krylov loop kernel by kernel, so every launch is bracketed by events)
+        prof, ms_prof = None, None
+        if prof_steps:
+            P.profile(True)
+            ev0.record(stream)
+            for i in range(prof_steps):
+                step(steps + i, False)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms_prof = ev0.elapsed_time(ev1)
+            prof = P.profile_read()
+            P.profile(False)
+        res = dict(ms=ms, iters=iters, prof=prof, ms_prof=ms_prof, launches=launches, clocks=ck,
+                   graph_used=graph_used, **val)
         del P
         return res
 
-    rec = run(strategy, args.steps, args.warmup, validate=True, profile_range=args.profile_range)
-    cg = run(parse("none"), args.steps, args.warmup, validate=True) if (args.compare_cg and strategy.recycles) else None
+    rec = run(strategy, args.steps, args.warmup, validate=True, profile_range=args.profile_range,
+              prof_steps=args.prof_steps)
+    cg = (run(parse("none"), args.steps, args.warmup, validate=True, prof_steps=args.prof_steps)
+          if (args.compare_cg and strategy.recycles) else None)
     e2e = run(strategy, args.steps, args.warmup, e2e=True) if args.e2e else None
     return dict(rec=rec, cg=cg, e2e=e2e, K=K, n_pix=n_pix, wl=wl, strategy=strategy)
 
@@ -278,6 +293,8 @@ def main():
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--pairs", type=int, default=0, help="use only the first PAIRS pairs (profiling cases)")
+    ap.add_argument("--prof-steps", type=int, default=2,
+                    help="extra steps timed kernel by kernel with CUDA events (roofline, kernel_ms)")
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (ncu --profile-from-start off)")
     args = ap.parse_args()
@@ -323,7 +340,10 @@ def main():
     ms = tmax(rec["ms"])
     value = K * world * args.steps / (ms / 1e3)
     # roofline of the dominant kernel: the fused Hessian action of the Krylov loop
-    hv = rec["prof"]["hvp"]
+    zero = {"ms": 0.0, "launches": 0, "pixels": 0}
+    profd = rec["prof"] or {k: zero for k in ["hvp", "hvp_multi", "grad", "jw", "krylov", "lbfgs", "gram", "gemm",
+                                               "dense", "other"]}
+    hv = profd["hvp"]
     fpp = hvp_flops_per_pixel(wl.n_filters, wl.filter_size, wl.pairs[0].blur_radius)
     bpp = hvp_bytes_per_pixel(wl.n_filters)
     avg_ms = hv["ms"] / max(1, hv["launches"])
@@ -332,7 +352,6 @@ def main():
     ck = rec["clocks"] or {}
     peak_tflops = FP32_FMA_LANES * 2 * 2070e6 / 1e12
     gbs = bpp * hv["pixels"] / max(1, hv["launches"]) / (avg_ms / 1e3) / 1e9
-    total_prof = sum(v["ms"] for v in rec["prof"].values())
     line = {
         "metric": metric, "value": value, "unit": "hypergradients/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -351,8 +370,12 @@ def main():
                      "flops_per_pixel": fpp, "pixels_per_launch": hv["pixels"] / max(1, hv["launches"]),
                      "avg_launch_ms": avg_ms, "hbm_gbs_algorithmic": gbs,
                      "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
-                     "share_of_step": hv["ms"] / max(1e-9, rec["ms"])},
-        "kernel_ms": {k: round(v["ms"], 3) for k, v in rec["prof"].items()},
+                     "share_of_step": hv["ms"] / max(1e-9, rec["ms_prof"] or 1e-9),
+                     "timing": f"CUDA events around every launch over {args.prof_steps} further steps "
+                               "(stream path)"},
+        "kernel_ms": {k: round(v["ms"], 3) for k, v in profd.items()},
+        "kernel_ms_steps": args.prof_steps, "profiled_ms_per_step": (rec["ms_prof"] or 0) / max(1, args.prof_steps),
+        "krylov_graph": rec["graph_used"],
         "gpu_launches": rec["launches"],
         "clocks": ck,
     }
@@ -360,9 +383,9 @@ def main():
         ms_cg = tmax(cg["ms"])
         line["plain_cg"] = {"value": K * world * args.steps / (ms_cg / 1e3), "ms_per_step": ms_cg / args.steps,
                             "krylov_iters_total": int(np.sum(cg["iters"])), "hg_rel_err_max": cg.get("hg_err_max"),
-                            "kernel_ms": {k: round(v["ms"], 3) for k, v in cg["prof"].items()},
-                            "hvp_avg_launch_ms": cg["prof"]["hvp"]["ms"] / max(1, cg["prof"]["hvp"]["launches"]),
-                            "hvp_pixels_per_launch": cg["prof"]["hvp"]["pixels"] / max(1, cg["prof"]["hvp"]["launches"])}
+                            "kernel_ms": ({k: round(v["ms"], 3) for k, v in cg["prof"].items()} if cg["prof"] else None),
+                            "hvp_avg_launch_ms": (cg["prof"]["hvp"]["ms"] / max(1, cg["prof"]["hvp"]["launches"])
+                                                  if cg["prof"] else None)}
     if out["e2e"] is not None:
         ms_e = tmax(out["e2e"]["ms"])
         h2d = 2 * n_pix * 4 + wl.n_params * 8

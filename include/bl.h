@@ -106,6 +106,9 @@ typedef struct {
   int32_t maxit;
   int32_t store_basis;   /* keep normalised residuals as V for the next bl_ritz_update */
   int32_t warm_start;    /* non-zero: w (in) is the initial guess; zero: start from 0 */
+  int32_t graph;         /* non-zero: run the iteration loop as one CUDA-graph launch (a WHILE node whose
+                            condition is set on the device), without host round trips; the stream path
+                            is used instead while profiling is enabled */
 } bl_krylov_opts;
 
 typedef enum { BL_RECYCLE_RITZ = 0, BL_RECYCLE_HRITZ = 1, BL_RECYCLE_RGSV = 2 } bl_recycle_kind;
@@ -213,6 +216,9 @@ int32_t bl_basis_size(const bl_problem* prob, int32_t pair);
  * size and precision (BL_EINVAL on any header mismatch or truncation). */
 bl_status bl_recycle_export(bl_problem* prob, int32_t pair, void* buf, size_t* bytes);
 bl_status bl_recycle_import(bl_problem* prob, int32_t pair, const void* buf, size_t bytes);
+
+/* 1 if the last bl_hessian_solve ran its loop as a CUDA graph (see bl_krylov_opts.graph), else 0. */
+int32_t bl_graph_used(const bl_problem* prob);
 
 /* Number of this library's kernel launches since the problem was created (host counter). */
 int64_t bl_launch_count(const bl_problem* prob);

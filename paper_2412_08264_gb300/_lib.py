@@ -45,7 +45,7 @@ class LbfgsOpts(C.Structure):
 class KrylovOpts(C.Structure):
     _fields_ = [("method", C.c_int32), ("stop", C.c_int32), ("tol", C.c_double),
                 ("relative", C.c_int32), ("maxit", C.c_int32), ("store_basis", C.c_int32),
-                ("warm_start", C.c_int32)]
+                ("warm_start", C.c_int32), ("graph", C.c_int32)]
 
 
 class RecycleOpts(C.Structure):
@@ -82,6 +82,7 @@ EXPORTS = {
     "bl_recycle_export": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_size_t)]),
     "bl_recycle_import": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_size_t]),
     "bl_launch_count": (C.c_int64, [C.c_void_p]),
+    "bl_graph_used": (C.c_int32, [C.c_void_p]),
     "bl_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "bl_profile_read": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                   C.POINTER(C.c_int64)]),

@@ -138,14 +138,15 @@ class Problem:
 
     def hessian_solve(self, w: torch.Tensor, g: Optional[torch.Tensor] = None, pairs=None, recycle: bool = True,
                       nsc: bool = False, tol: float = 1e-4, relative: bool = True, maxit: int = 2000,
-                      store_basis: bool = True, warm_start: bool = True, nsc_scale=None, allow_noconv=False):
+                      store_basis: bool = True, warm_start: bool = True, nsc_scale=None, allow_noconv=False,
+                      graph: bool = True):
         pa, n, idx = self._pairs(pairs)
         self._check_images(w, idx)
         if g is not None:
             self._check_images(g, idx)
         o = L.KrylovOpts(L.BL_SOLVE_RCG if recycle else L.BL_SOLVE_CG, L.BL_STOP_NSC if nsc else L.BL_STOP_RESID,
                          float(tol), 1 if relative else 0, int(maxit), 1 if store_basis else 0,
-                         1 if warm_start else 0)
+                         1 if warm_start else 0, 1 if graph else 0)
         sc = None
         if nsc_scale is not None:
             sc = (C.c_double * n)(*[float(v) for v in nsc_scale])
@@ -187,6 +188,9 @@ class Problem:
     def recycle_import(self, pair: int, data: bytes):
         buf = C.create_string_buffer(data, len(data))
         L.check(self.lib.bl_recycle_import(self.h, int(pair), buf, len(data)), "bl_recycle_import")
+
+    def graph_used(self) -> bool:
+        return bool(self.lib.bl_graph_used(self.h))
 
     def launch_count(self) -> int:
         return int(self.lib.bl_launch_count(self.h))

@@ -78,6 +78,22 @@ struct ProfEvent {
   int cls;
 };
 
+// Cached CUDA graph of the recycled-CG loop (a WHILE node around one iteration).
+struct KrylovGraphKey {
+  bool fused;
+  int store, nsc;
+  const void *tpart, *cpart, *V;
+  bool operator==(const KrylovGraphKey& o) const {
+    return fused == o.fused && store == o.store && nsc == o.nsc && tpart == o.tpart && cpart == o.cpart && V == o.V;
+  }
+};
+struct KrylovGraph {
+  KrylovGraphKey key{};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int body_kernels = 0;
+};
+
 struct PairHost {
   int h, w;
   long long n, off;
@@ -124,6 +140,14 @@ struct bl_problem {
   int* d_active = nullptr;  // generic per-pair mask
   int* d_cols = nullptr;    // per-pair column counts for multi-column kernels
   int* d_flag = nullptr;    // any-active flag (device)
+  int* d_zero = nullptr;    // K zeros (per-pair "none" flags)
+  int* d_loop = nullptr;    // graph loop counter and cap
+  cudaStream_t cstream = nullptr;   // private stream used only to capture graphs
+  bl::KrylovGraph* kgraph = nullptr;
+  bool graph_failed = false;        // graph capture unavailable: the stream path is used
+  bool graph_used = false;          // the last solve ran as a graph launch
+  bool capturing = false;           // a graph capture is recording the launches
+  std::string graph_error;          // why the graph capture failed, if it did
   int* h_flag = nullptr;    // pinned host mirror
   std::vector<int> s_k, kb_k, hz_k, head_k;
 
@@ -187,11 +211,16 @@ bl_status launch_forward(bl_problem* P, const void* x, void* out, const int* mas
 // J w for `cols` columns: per-pair results (K x cols x p doubles, [k][col][m]) in out.
 bl_status launch_jw(bl_problem* P, const void* in, int mult, int cols, const int* mask, double* out);
 bl_status load_theta(bl_problem* P, const double* theta);
+// Raise the dynamic shared-memory limits of the stencil kernels this problem launches (done once at
+// creation, so that graph capture never has to change function attributes).
+bl_status prepare_kernels(bl_problem* P);
 
 // ---- krylov.cu ----
 bl_status run_hessian_solve(bl_problem* P, const int* mask_host, const bl_krylov_opts* o,
                             const void* g_batched, const double* nsc_scale_batched,
                             std::vector<bl_solve_info>& info);
+
+void destroy_krylov_graph(bl_problem* P);
 
 // ---- recycle.cu ----
 bl_status run_ritz_update(bl_problem* P, const std::vector<int>& mask_host,

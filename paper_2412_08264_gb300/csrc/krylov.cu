@@ -7,8 +7,8 @@
 //   end    w += U z
 // which is CG on P H P (P = I - C C^T) with the recycle-space coefficients gathered in z, so that
 // g - H (w + U z) = r and C^T r = 0 hold throughout (the augmentation of Algorithm 3 carried
-// over to CG).  The hypergradient-error estimate of eq. (4.2), ||Z^T r||, is carried by the
-// recurrence Z^T r' = Z^T r - alpha (Z^T q - (Z^T C) c).
+// over to CG).  The hypergradient-error estimate of eq. (4.2), ||Z^T r||, is formed from the
+// updated residual in the same pass that updates it.
 //
 // All pairs advance together: vectors are batched over pairs, every per-pair scalar (rho, alpha,
 // beta, the s-vectors c, z, Z^T r) lives on the device in FP64, and each kernel skips the pairs
@@ -252,22 +252,20 @@ __global__ void k_dots(KrylovArgs a, const T* p, const T* q, const T* C, const T
   }
 }
 
-// alpha, c = C^T q, z -= alpha c, Z^T r -= alpha (Z^T q - Z^T C c); breakdown check
+// alpha, c = C^T q, z -= alpha c; breakdown check
 __global__ void k_scalar1(KrylovArgs a, int use_tiles) {
-  __shared__ double sh[2 * 64 + 1];
+  __shared__ double sh[65];
   __shared__ double alpha_s;
   const int k = blockIdx.x;
   if (!a.st[k].active) return;
   const PairDev pr = a.pairs[k];
   const int s = a.s_k[k];
-  const int nz = a.hasz[k] ? s : 0;
-  const int ncomp = 1 + 2 * a.SMAX;
+  const int ncomp = use_tiles ? 1 + 2 * a.SMAX : 1 + 2 * a.SMAX;
   const double* part = use_tiles ? a.tpart : a.cpart;
   const int beg = use_tiles ? pr.tbeg : pr.cbeg, end = use_tiles ? pr.tend : pr.cend;
-  for (int m = threadIdx.x; m < 1 + s + nz; m += blockDim.x) {
-    const int slot = m <= s ? m : m - s + a.SMAX;
+  for (int m = threadIdx.x; m < 1 + s; m += blockDim.x) {
     double t = 0.0;
-    for (int u = beg; u < end; ++u) t += part[(size_t)u * ncomp + slot];
+    for (int u = beg; u < end; ++u) t += part[(size_t)u * ncomp + m];
     sh[m] = t;
   }
   __syncthreads();
@@ -290,27 +288,27 @@ __global__ void k_scalar1(KrylovArgs a, int use_tiles) {
     a.c[k * a.SMAX + m] = sh[1 + m];
     a.zc[k * a.SMAX + m] -= al * sh[1 + m];
   }
-  for (int m = threadIdx.x; m < nz; m += blockDim.x) {
-    double ztcc = 0.0;
-    for (int j = 0; j < s; ++j) ztcc += a.ztc[((size_t)k * a.SMAX + m) * a.SMAX + j] * sh[1 + j];
-    a.e[k * a.SMAX + m] = sh[1 + s + m];
-    a.ztr[k * a.SMAX + m] -= al * (sh[1 + s + m] - ztcc);
-  }
 }
 
-// w += alpha p; V[:, it] = r / ||r||; r -= alpha (q - C c); partial rho' = r^T r
+// w += alpha p; V[:, it] = r / ||r||; r -= alpha (q - C c); partials [0] rho' = r^T r and, for the
+// NSC rule, [1..nz] Z^T r (read back from the r values this thread just wrote)
 template <typename T>
-__global__ void k_update(KrylovArgs a, T* w, T* r, const T* p, const T* q, const T* C, T* V, int store) {
-  __shared__ double red[40];
+__global__ void k_update(KrylovArgs a, T* w, T* r, const T* p, const T* q, const T* C, const T* Z, T* V,
+                         int store, int nsc) {
+  __shared__ double red[8 * 65];
   __shared__ T cs[64];
   const ChunkDev ch = a.chunks[blockIdx.x];
   const SolveState S = a.st[ch.pair];
   if (!S.active) return;
   const PairDev pr = a.pairs[ch.pair];
   const int s = a.s_k[ch.pair];
+  const int nz = (nsc && a.hasz[ch.pair]) ? s : 0;
+  const int ncomp = 1 + a.SMAX;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if ((int)threadIdx.x < s) cs[threadIdx.x] = (T)a.c[ch.pair * a.SMAX + threadIdx.x];
   __syncthreads();
   const T* Cb = C + pr.off * a.SMAX;
+  const T* Zb = Z + pr.off * a.SMAX;
   T* Vc = store ? V + pr.off * a.KMAX + (long long)(S.iters % a.KMAX) * pr.n : nullptr;
   const T inv_nr = (T)(1.0 / sqrt(S.rho));
   const T al = (T)S.alpha;
@@ -326,41 +324,65 @@ __global__ void k_update(KrylovArgs a, T* w, T* r, const T* p, const T* q, const
     r[gi] = rn;
     rho.add(rn * rn);
   }
-  const double tot = block_total<kChunkThreads>(rho, red);
-  if (threadIdx.x == 0) a.cpart[blockIdx.x] = tot;
+  {
+    const double v = warp_total(rho);
+    if (lane == 0) red[wid * 65] = v;
+  }
+  for (int m = 0; m < nz; ++m) {
+    Accum<T> acc;
+    for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
+      const long long li = ch.start + t;
+      acc.add(Zb[(long long)m * pr.n + li] * r[pr.off + li]);
+    }
+    const double v = warp_total(acc);
+    if (lane == 0) red[wid * 65 + 1 + (m & 63)] = v;
+    if ((m & 63) == 63 || m == nz - 1) {
+      __syncthreads();
+      const int base = (m & ~63);
+      flush_components<kChunkThreads>(red + 1, m - base + 1, a.cpart + (size_t)blockIdx.x * ncomp + 1 + base);
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  flush_components<kChunkThreads>(red, 1, a.cpart + (size_t)blockIdx.x * ncomp);
 }
 
-// rho', beta, stopping test
+// rho', Z^T r, beta, stopping test
 __global__ void k_scalar2(KrylovArgs a, int stop_nsc, int* flag) {
-  __shared__ double sh;
+  __shared__ double sh[65];
   const int k = blockIdx.x;
   if (!a.st[k].active) return;
   const PairDev pr = a.pairs[k];
-  if (threadIdx.x == 0) {
+  const int s = a.s_k[k];
+  const int nz = (stop_nsc && a.hasz[k]) ? s : 0;
+  const int ncomp = 1 + a.SMAX;
+  for (int m = threadIdx.x; m <= nz; m += blockDim.x) {
     double t = 0.0;
-    for (int u = pr.cbeg; u < pr.cend; ++u) t += a.cpart[u];
-    sh = t;
+    for (int u = pr.cbeg; u < pr.cend; ++u) t += a.cpart[(size_t)u * ncomp + m];
+    sh[m] = t;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     SolveState S = a.st[k];
-    const int s = a.s_k[k];
-    const int nz = a.hasz[k] ? s : 0;
-    S.rho_new = sh;
-    S.beta = sh / S.rho;
-    S.rho = sh;
+    const double rho_new = sh[0];
+    S.rho_new = rho_new;
+    S.beta = rho_new / S.rho;
+    S.rho = rho_new;
     S.iters += 1;
-    if (stop_nsc && nz > 0) {
+    if (nz > 0) {
       double z2 = 0.0;
-      for (int m = 0; m < nz; ++m) z2 += a.ztr[k * a.SMAX + m] * a.ztr[k * a.SMAX + m];
+      for (int m = 0; m < nz; ++m) {
+        a.ztr[k * a.SMAX + m] = sh[1 + m];
+        z2 += sh[1 + m] * sh[1 + m];
+      }
       S.est = sqrt(z2);
     } else {
-      S.est = sqrt(sh);
+      S.est = sqrt(rho_new);
     }
-    if (!isfinite(sh)) {
+    if (!isfinite(rho_new)) {
       S.active = 0;
       S.status = BL_EBREAKDOWN;
-    } else if (S.est < S.tol || sh == 0.0) {
+    } else if (S.est < S.tol || rho_new == 0.0) {
       S.active = 0;
     } else if (S.iters >= S.maxit) {
       S.active = 0;
@@ -404,6 +426,75 @@ __global__ void k_finalize(KrylovArgs a, T* w, const T* U, const int* mask) {
   }
 }
 
+// WHILE-node condition: another body run while some pair is active and the hard cap is not reached.
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, const int* flag, int* loop) {
+  const int ran = ++loop[0];
+  cudaGraphSetConditional(h, (*flag > 0 && ran < loop[1]) ? 1u : 0u);
+}
+
+template <typename F>
+static bl_status build_krylov_graph(bl_problem* P, const KrylovGraphKey& key, F&& iteration) {
+  destroy_krylov_graph(P);
+  if (!P->cstream) BL_CUDA_TRY(cudaStreamCreateWithFlags(&P->cstream, cudaStreamNonBlocking));
+  KrylovGraph* G = new KrylovGraph();
+  G->key = key;
+  P->kgraph = G;
+  BL_CUDA_TRY(cudaGraphCreate(&G->graph, 0));
+  cudaGraphConditionalHandle h;
+  BL_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, G->graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  BL_CUDA_TRY(cudaGraphAddNode(&node, G->graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  // capture one iteration into the body on a private stream (capture only records)
+  cudaStream_t user = P->stream;
+  const bool prof = P->prof;
+  const int64_t l0 = P->launches;
+  P->stream = P->cstream;
+  P->prof = false;
+  P->capturing = true;
+  bl_status st = BL_OK;
+  cudaError_t e = cudaStreamBeginCaptureToGraph(P->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    st = iteration();
+    if (st == BL_OK) {
+      k_loop_cond<<<1, 1, 0, P->stream>>>(h, P->d_flag, P->d_loop);
+      ++P->launches;
+      e = cudaGetLastError();
+    }
+    cudaGraph_t out = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(P->stream, &out);
+    if (e == cudaSuccess) e = e2;
+  }
+  G->body_kernels = (int)(P->launches - l0);
+  P->launches = l0;
+  P->stream = user;
+  P->prof = prof;
+  P->capturing = false;
+  if (st != BL_OK) {
+    destroy_krylov_graph(P);
+    return st;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&G->exec, G->graph, 0);
+  if (e != cudaSuccess) {
+    destroy_krylov_graph(P);
+    return fail(BL_ECUDA, std::string("Krylov graph: ") + cudaGetErrorString(e));
+  }
+  return BL_OK;
+}
+
+void destroy_krylov_graph(bl_problem* P) {
+  if (!P->kgraph) return;
+  if (P->kgraph->exec) cudaGraphExecDestroy(P->kgraph->exec);
+  if (P->kgraph->graph) cudaGraphDestroy(P->kgraph->graph);
+  delete P->kgraph;
+  P->kgraph = nullptr;
+}
+
 __global__ void k_copy_active(const SolveState* st, int* out, int K) {
   for (int k = threadIdx.x; k < K; k += blockDim.x) out[k] = st[k].active;
 }
@@ -421,6 +512,7 @@ static bl_status solve_impl(bl_problem* P, const int* mask_host, const bl_krylov
   }
   int* d_seff = P->d_cols;          // reuse: per-pair ints
   int* d_hz = P->d_cols + K;
+  const int* d_nohz = P->d_zero;    // zeros: no Z^T q in the Hessian-action epilogue
   BL_CUDA_TRY(cudaMemcpyAsync(d_seff, s_eff.data(), K * sizeof(int), cudaMemcpyHostToDevice, P->stream));
   BL_CUDA_TRY(cudaMemcpyAsync(d_hz, hz_eff.data(), K * sizeof(int), cudaMemcpyHostToDevice, P->stream));
   double* d_scale = P->vals;        // K doubles
@@ -483,36 +575,68 @@ static bl_status solve_impl(bl_problem* P, const int* mask_host, const bl_krylov
   BL_CUDA_TRY(cudaStreamSynchronize(P->stream));
 
   // ---- iterations ----
-  // the per-pair `active` flags gate every kernel; the host only polls the any-active count
+  // the per-pair `active` flags gate every kernel; the loop ends when no pair is active
   int* d_itmask = P->d_active + K; // per-pair active copy for the stencil mask
-  for (int it = 0; it < o->maxit && *P->h_flag > 0; ++it) {
-    // stencil mask = active flags of this iteration
+  const int store = (o->store_basis && P->KMAX > 0) ? 1 : 0;
+  const int nsc = o->stop == BL_STOP_NSC ? 1 : 0;
+  auto iteration = [&]() -> bl_status {
     {
       ProfScope ps(P, BL_KC_KRYLOV);
       k_copy_active<<<1, 128, 0, P->stream>>>(P->st, d_itmask, K);
       BL_LAUNCH_CHECK(P);
     }
-    st = launch_hvp(P, p, q, 0, 0, d_itmask, fused ? d_seff : nullptr, fused ? d_hz : nullptr);
-    if (st != BL_OK) return st;
-    {
+    bl_status s2 = launch_hvp(P, p, q, 0, 0, d_itmask, fused ? d_seff : nullptr, fused ? d_nohz : nullptr);
+    if (s2 != BL_OK) return s2;
     ProfScope ps(P, BL_KC_KRYLOV);
     if (!fused) {
-      k_dots<T><<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a, p, q, C, Z);
+      KrylovArgs a0 = a;
+      a0.hasz = d_nohz;   // the NSC sums come from the update pass
+      k_dots<T><<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a0, p, q, C, Z);
       BL_LAUNCH_CHECK(P);
     }
     k_scalar1<<<K, 128, 0, P->stream>>>(a, fused ? 1 : 0);
     BL_LAUNCH_CHECK(P);
-    k_update<T><<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a, w, r, p, q, C, (T*)P->V,
-                                                               (o->store_basis && P->KMAX > 0) ? 1 : 0);
+    k_update<T><<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a, w, r, p, q, C, Z, (T*)P->V, store, nsc);
     BL_LAUNCH_CHECK(P);
     BL_CUDA_TRY(cudaMemsetAsync(P->d_flag, 0, sizeof(int), P->stream));
-    k_scalar2<<<K, 32, 0, P->stream>>>(a, o->stop == BL_STOP_NSC ? 1 : 0, P->d_flag);
+    k_scalar2<<<K, 32, 0, P->stream>>>(a, nsc, P->d_flag);
     BL_LAUNCH_CHECK(P);
     k_pupdate<T><<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a, r, p);
     BL_LAUNCH_CHECK(P);
+    return BL_OK;
+  };
+  bool use_graph = *P->h_flag > 0 && o->graph && !P->prof && !P->graph_failed;
+  if (use_graph) {
+    const KrylovGraphKey key{fused, store, nsc, P->tpart, P->cpart, P->V};
+    if (!P->kgraph || !(P->kgraph->key == key)) {
+      if (build_krylov_graph(P, key, iteration) != BL_OK) {
+        // the stream path below runs the same kernels; remember not to retry the capture
+        P->graph_error = error_copy();
+        P->graph_failed = true;
+        use_graph = false;
+        (void)cudaGetLastError();
+      }
     }
-    BL_CUDA_TRY(cudaMemcpyAsync(P->h_flag, P->d_flag, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+  }
+  P->graph_used = use_graph;
+  if (use_graph) {
+    // one graph launch runs the whole loop: a WHILE node whose body is one iteration, its
+    // condition set on the device from the any-active count (the iteration caps of every pair
+    // bound it; a loop counter adds a hard cap of maxit + 1 body runs)
+    const int cap[2] = {0, o->maxit + 1};
+    BL_CUDA_TRY(cudaMemcpyAsync(P->d_loop, cap, sizeof(cap), cudaMemcpyHostToDevice, P->stream));
+    BL_CUDA_TRY(cudaGraphLaunch(P->kgraph->exec, P->stream));
+    int ran = 0;
+    BL_CUDA_TRY(cudaMemcpyAsync(&ran, P->d_loop, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
     BL_CUDA_TRY(cudaStreamSynchronize(P->stream));
+    P->launches += (int64_t)ran * P->kgraph->body_kernels + 1;
+  } else {
+    for (int it = 0; it < o->maxit && *P->h_flag > 0; ++it) {
+      st = iteration();
+      if (st != BL_OK) return st;
+      BL_CUDA_TRY(cudaMemcpyAsync(P->h_flag, P->d_flag, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+      BL_CUDA_TRY(cudaStreamSynchronize(P->stream));
+    }
   }
   {
     ProfScope ps(P, BL_KC_KRYLOV);

@@ -97,6 +97,8 @@ const char* bl_last_error(void) {
 
 int64_t bl_launch_count(const bl_problem* P) { return P ? P->launches : 0; }
 
+int32_t bl_graph_used(const bl_problem* P) { return (P && P->graph_used) ? 1 : 0; }
+
 static bl_status prof_collect(bl_problem* P) {
   BL_CUDA_TRY(cudaStreamSynchronize(P->stream));
   for (size_t i = 0; i < P->prof_used; ++i) {
@@ -163,12 +165,14 @@ bl_status bl_set_stream(bl_problem* P, void* s) {
 void bl_problem_destroy(bl_problem* P) {
   if (!P) return;
   cudaStreamSynchronize(P->stream);
+  destroy_krylov_graph(P);
+  if (P->cstream) cudaStreamDestroy(P->cstream);
   void* bufs[] = {P->d_pairs, P->d_tiles, P->d_chunks, P->y, P->xstar, P->xhat, P->fu, P->fd, P->theta,
                   P->taps_f, P->taps_d, P->ealpha, P->r, P->pv, P->q, P->w, P->g, P->tmp, P->U, P->C, P->Z,
                   P->V, P->W, P->Wt, P->HWt, P->st, P->c, P->zc, P->e, P->ztr, P->ztc, P->d_s, P->d_hasz,
                   P->d_active, P->d_cols, P->d_flag, P->dG, P->dT, P->dJ, P->dY, P->dY2, P->dY3, P->d_tk,
                   P->lx, P->lg, P->ld, P->lxt, P->lgt, P->lq, P->S, P->Yh, P->lst, P->tpart, P->cpart, P->vals,
-                  P->d_pix};
+                  P->d_pix, P->d_zero, P->d_loop};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (P->h_flag) cudaFreeHost(P->h_flag);
@@ -320,6 +324,8 @@ bl_status bl_problem_create(const bl_pair_desc* pairs, int32_t K, const bl_reg_d
   BL_ALLOC(dalloc((void**)&P->d_cols, 2 * K * sizeof(int)));
   BL_ALLOC(dalloc((void**)&P->d_tk, 2 * K * sizeof(int)));
   BL_ALLOC(dalloc((void**)&P->d_flag, sizeof(int)));
+  BL_ALLOC(dalloc((void**)&P->d_zero, K * sizeof(int)));
+  BL_ALLOC(dalloc((void**)&P->d_loop, 2 * sizeof(int)));
   const size_t tm2 = (size_t)K * P->TM * P->TM;
   BL_ALLOC(dalloc((void**)&P->dG, tm2 * sizeof(double)));
   BL_ALLOC(dalloc((void**)&P->dT, 2 * tm2 * sizeof(double)));
@@ -345,12 +351,17 @@ bl_status bl_problem_create(const bl_pair_desc* pairs, int32_t K, const bl_reg_d
   e = e == cudaSuccess ? cpy(P->xstar, xstar_packed, n * P->esz, cudaMemcpyDeviceToDevice) : e;
   e = e == cudaSuccess ? cudaMemsetAsync(P->d_s, 0, K * sizeof(int), P->stream) : e;
   e = e == cudaSuccess ? cudaMemsetAsync(P->d_hasz, 0, K * sizeof(int), P->stream) : e;
+  e = e == cudaSuccess ? cudaMemsetAsync(P->d_zero, 0, K * sizeof(int), P->stream) : e;
   e = e == cudaSuccess ? cudaMemsetAsync(P->ztc, 0, (size_t)K * P->SMAX * P->SMAX * sizeof(double), P->stream) : e;
   e = e == cudaSuccess ? cudaMemsetAsync(P->xhat, 0, n * P->esz, P->stream) : e;
   e = e == cudaSuccess ? cudaStreamSynchronize(P->stream) : e;
   if (e != cudaSuccess) {
     bl_problem_destroy(P);
     return fail(BL_ECUDA, std::string("problem set-up: ") + cudaGetErrorString(e));
+  }
+  if ((st = prepare_kernels(P)) != BL_OK) {
+    bl_problem_destroy(P);
+    return st;
   }
   *out = P;
   return BL_OK;

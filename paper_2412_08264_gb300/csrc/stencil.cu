@@ -342,10 +342,25 @@ __global__ void __launch_bounds__(kStencilThreads, sizeof(T) == 4 ? 2 : 1) k_foe
         for (int i = 0; i < vh; ++i)
           for (int j = lane; j < vw; j += 32) acc.add(vs[(i + kHalo) * VD + j + kHalo] * qs[i * TILE + j]);
       } else {
+        // 8 rows x 2 lane positions of loads are issued before their products are accumulated,
+        // so a warp keeps 16 global loads in flight instead of one
         const T* col = cc <= s ? Cb + (long long)(cc - 1) * pr.n : Zb + (long long)(cc - 1 - s) * pr.n;
-        for (int i = 0; i < vh; ++i) {
-          const T* row = col + (long long)(oy + i) * w + ox;
-          for (int j = lane; j < vw; j += 32) acc.add(row[j] * qs[i * TILE + j]);
+        for (int i0 = 0; i0 < vh; i0 += 8) {
+          T v[8][2];
+#pragma unroll
+          for (int ii = 0; ii < 8; ++ii)
+#pragma unroll
+            for (int jj = 0; jj < 2; ++jj) {
+              const int i = i0 + ii, j = lane + 32 * jj;
+              v[ii][jj] = (i < vh && j < vw) ? col[(long long)(oy + i) * w + ox + j] : T(0);
+            }
+#pragma unroll
+          for (int ii = 0; ii < 8; ++ii)
+#pragma unroll
+            for (int jj = 0; jj < 2; ++jj) {
+              const int i = i0 + ii, j = lane + 32 * jj;
+              if (i < vh && j < vw) acc.add(v[ii][jj] * qs[i * TILE + j]);
+            }
         }
       }
       const double v = warp_total(acc);
@@ -722,8 +737,9 @@ static bl_status hvp_foe(bl_problem* P, const void* in, void* out, int mult, int
 #define BL_HVP_CASE(FF)                                                                           \
   case FF: {                                                                                      \
     size_t sm = StencilSmem<T, FF>::bytes(P->N);                                                  \
-    BL_CUDA_TRY(cudaFuncSetAttribute(k_foe_stencil<T, FF, kModeHvp>,                              \
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));      \
+    if (!P->capturing)                                                                            \
+      BL_CUDA_TRY(cudaFuncSetAttribute(k_foe_stencil<T, FF, kModeHvp>,                            \
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));    \
     k_foe_stencil<T, FF, kModeHvp><<<grid, kStencilThreads, sm, P->stream>>>(a);                  \
     break;                                                                                        \
   }
@@ -838,8 +854,9 @@ static bl_status grad_impl(bl_problem* P, const void* x, void* grad, const int* 
 #define BL_GRAD_CASE(FF)                                                                          \
   case FF: {                                                                                      \
     size_t sm = StencilSmem<T, FF>::bytes(P->N);                                                  \
-    BL_CUDA_TRY(cudaFuncSetAttribute(k_foe_stencil<T, FF, kModeGrad>,                             \
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));      \
+    if (!P->capturing)                                                                            \
+      BL_CUDA_TRY(cudaFuncSetAttribute(k_foe_stencil<T, FF, kModeGrad>,                           \
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));    \
     k_foe_stencil<T, FF, kModeGrad><<<grid, kStencilThreads, sm, P->stream>>>(a);                 \
     break;                                                                                        \
   }
@@ -924,8 +941,9 @@ static bl_status jw_impl(bl_problem* P, const void* in, int mult, int cols, cons
     constexpr int RS = tile_out(FF) + 2 * (FF / 2);                                               \
     size_t sm = (2 * (size_t)RS * RS + 2 * 16 * kStencilThreads +                                 \
                  (size_t)(FF * FF + 1) * kStencilThreads) * sizeof(T);                            \
-    BL_CUDA_TRY(cudaFuncSetAttribute(k_foe_jw<T, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                     (int)sm));                                                   \
+    if (!P->capturing)                                                                            \
+      BL_CUDA_TRY(cudaFuncSetAttribute(k_foe_jw<T, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                       (int)sm));                                                 \
     k_foe_jw<T, FF><<<grid, kStencilThreads, sm, P->stream>>>(                                    \
         P->d_pairs, P->d_tiles, P->n_tiles, (const T*)in, mult, P->d_cols, (const T*)P->xhat,     \
         (const T*)P->fu, taps, P->ealpha, P->N, (T)P->reg.phi_eps, P->reg.phi, P->n_tot, mask,    \
@@ -947,6 +965,37 @@ static bl_status jw_impl(bl_problem* P, const void* in, int mult, int cols, cons
 bl_status launch_jw(bl_problem* P, const void* in, int mult, int cols, const int* mask, double* out) {
   return P->prec == BL_FP32 ? jw_impl<float>(P, in, mult, cols, mask, out)
                             : jw_impl<double>(P, in, mult, cols, mask, out);
+}
+
+}  // namespace bl
+
+namespace bl {
+
+template <typename T, int F>
+static bl_status prepare_one(bl_problem* P) {
+  const size_t sm = StencilSmem<T, F>::bytes(P->N);
+  BL_CUDA_TRY(cudaFuncSetAttribute(k_foe_stencil<T, F, kModeHvp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  BL_CUDA_TRY(cudaFuncSetAttribute(k_foe_stencil<T, F, kModeGrad>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  constexpr int RS = tile_out(F) + 2 * (F / 2);
+  const size_t smj = (2 * (size_t)RS * RS + 2 * 16 * kStencilThreads + (size_t)(F * F + 1) * kStencilThreads) * sizeof(T);
+  BL_CUDA_TRY(cudaFuncSetAttribute(k_foe_jw<T, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smj));
+  return BL_OK;
+}
+
+template <typename T>
+static bl_status prepare_t(bl_problem* P) {
+  switch (P->F) {
+    case 1: return prepare_one<T, 1>(P);
+    case 3: return prepare_one<T, 3>(P);
+    case 5: return prepare_one<T, 5>(P);
+    case 7: return prepare_one<T, 7>(P);
+    default: return fail(BL_EINVAL, "unsupported filter size");
+  }
+}
+
+bl_status prepare_kernels(bl_problem* P) {
+  if (P->reg.kind != BL_REG_FOE) return BL_OK;
+  return P->prec == BL_FP32 ? prepare_t<float>(P) : prepare_t<double>(P);
 }
 
 }  // namespace bl

@@ -48,6 +48,7 @@ bl_status dalloc(void** ptr, size_t bytes) {
 
 bl_status ensure_tpart(bl_problem* P, size_t doubles) {
   if (doubles <= P->tpart_cap) return BL_OK;
+  destroy_krylov_graph(P);
   if (P->tpart) {
     cudaStreamSynchronize(P->stream);
     cudaFree(P->tpart);
@@ -60,6 +61,7 @@ bl_status ensure_tpart(bl_problem* P, size_t doubles) {
 
 bl_status ensure_cpart(bl_problem* P, size_t doubles) {
   if (doubles <= P->cpart_cap) return BL_OK;
+  destroy_krylov_graph(P);
   if (P->cpart) {
     cudaStreamSynchronize(P->stream);
     cudaFree(P->cpart);

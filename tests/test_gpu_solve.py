@@ -166,3 +166,25 @@ def test_status_codes():
     with pytest.raises(L.BLError) as e:
         P.hessian_solve(P.zeros(), g=bad, recycle=False, warm_start=False)   # non-finite right-hand side
     assert e.value.status == L.BL_EBREAKDOWN
+
+
+def test_graph_loop_matches_stream_loop():
+    """The recycled-CG loop launched as one CUDA graph (WHILE node, device-side condition) gives the
+    same iterations and bit-identical solutions as the host-polled stream loop."""
+    wl = small_wl(sizes=((64, 70), (33, 40), (90, 31)), N=3, seed=17)
+    P, prob, dt = make(wl, "fp32", max_recycle=6, max_basis=40)
+    th = r32(wl.theta0)
+    xs = [r32(x + 0.01) for x in wl.x_star]
+    P.set_point(torch.tensor(th, dtype=torch.float64, device=DEV), packed(xs, dt))
+    w0 = P.zeros()
+    P.hessian_solve(w0, recycle=False, tol=1e-4, store_basis=True, graph=False)
+    P.ritz_update("RGen-L(R)", 6)
+    outs = []
+    for graph in (False, True, True):
+        w = P.zeros()
+        info = P.hessian_solve(w, recycle=True, tol=1e-6, store_basis=False, graph=graph)
+        assert P.graph_used() == graph
+        outs.append(([i["iters"] for i in info], w.cpu().numpy()))
+    for iters, w in outs[1:]:
+        assert iters == outs[0][0]
+        assert np.array_equal(w, outs[0][1])
