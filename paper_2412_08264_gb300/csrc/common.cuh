@@ -68,8 +68,10 @@ struct SolveState {
 };
 
 // Per-pair L-BFGS state.
+// The (s, y) history is a ring of m + 1 slots: the newest `hist_count` <= m pairs are valid and
+// `hist_head` (the next slot written) never holds one of them.
 struct LbfgsState {
-  double f, f_trial, gtd, t, gnorm, gtol, rho_hist[kMaxHistory], a_hist[kMaxHistory], gamma;
+  double f, f_trial, gtd, t, gnorm, gtol, gamma;
   int active, accepted, iters, status, hist_count, hist_head, backtracks, pad;
 };
 
@@ -157,7 +159,9 @@ struct bl_problem {
 
   // L-BFGS
   void *lx = nullptr, *lg = nullptr, *ld = nullptr, *lxt = nullptr, *lgt = nullptr, *lq = nullptr;
-  void *S = nullptr, *Yh = nullptr;
+  void *S = nullptr, *Yh = nullptr;    // n x (MH + 1) ring of s and y columns
+  double *lsy = nullptr, *lyy = nullptr; // K x (MH + 1)^2: s_i^T y_j and y_i^T y_j by slot
+  double *lcs = nullptr, *lcy = nullptr; // K x (MH + 1): direction coefficients by slot
   bl::LbfgsState* lst = nullptr;
   int MH = 0;
 

@@ -1,7 +1,13 @@
 // Batched lower-level solve: L-BFGS with Armijo backtracking (Section 5.1), all pairs together.
 //
-// Per iteration and pair: the two-loop recursion over the m most recent (s, y) pairs with
-// initial scaling gamma = s^T y / y^T y of the newest pair (1 before any pair exists), a
+// Per iteration and pair: the L-BFGS direction d = -H g over the m most recent (s, y) pairs with
+// initial scaling gamma = s^T y / y^T y of the newest pair (1 before any pair exists).  The
+// direction is formed in the compact representation of the L-BFGS matrix (Byrd, Nocedal and
+// Schnabel 1994), algebraically the two-loop recursion's result:
+//   H g = gamma g + S R^{-T} ((D + gamma Y^T Y) R^{-1} S^T g - gamma Y^T g) - gamma Y R^{-1} S^T g,
+// R the upper triangle of S^T Y and D its diagonal (columns oldest first), so one pass forms the 4m
+// dot products S^T g, Y^T g, S^T y_new, Y^T y_new, an m x m FP64 solve per pair gives the
+// coefficients, and a second pass forms d.  Then a
 // descent check (restart from -grad if g^T d >= 0), Armijo backtracking with c1 = 1e-4 from
 // step 1 halving the step (an optional slack eps |Phi| on the sufficient-decrease test lets FP32
 // runs accept steps whose change is below FP32 resolution of Phi), and the pair update only
@@ -19,67 +25,153 @@ struct LbArgs {
   const PairDev* pairs;
   const ChunkDev* chunks;
   LbfgsState* st;
-  int MH;
-  double* cpart;    // per chunk, 4 components
-  double* acoef;    // K x MH: a_i of the first loop, read by the second
+  int MH;             // memory m; the ring holds m + 1 slots
+  double* cpart;      // per chunk partial sums
+  double *sy, *yy;    // K x (m + 1)^2 by slot
+  double *cs, *cy;    // K x (m + 1) direction coefficients by slot
 };
 
-__device__ __forceinline__ int lb_slot(const LbfgsState& S, int i, int MH) {
-  return (S.hist_head - 1 - i + 2 * MH) % MH;
+// Slot of the i-th oldest valid pair (ring of RS = m + 1 slots).
+__device__ __forceinline__ int lb_age_slot(const LbfgsState& S, int i, int RS) {
+  return (S.hist_head - S.hist_count + i + 2 * RS) % RS;
 }
 
-// X op= ... : mode 0: X = src (copy); 1: X += coef Y_i; 2: X = gamma * X; 3: X += coef S_i;
-// 5: X = -src.  The coefficient of modes 1 and 3 comes from the partial sums of the previous
-// launch (part_in, one per chunk), which every block reduces over its own pair's chunks in the
-// same order:  mode 1  a_i = rho_i S_i^T q,  coef = -a_i   (a_i kept for the second loop);
-//              mode 3  b_i = rho_i Y_i^T d,  coef = a_i - b_i.
-// Then the partial dot D^T X with D = dotm[:, slot(idot)] (idot >= 0) or D = dotv (idot == -2)
-// goes to part_out (a different buffer from part_in).
+// Pass A: per chunk partial sums [4 * RS * chunk + 4 i + q] for the i-th oldest pair, q = 0..3:
+// s_i^T g, y_i^T g, s_i^T y_new, y_i^T y_new (y_new: the newest stored y).
 template <typename T>
-__global__ void k_lb_step(LbArgs a, T* X, const T* src, int mode, const T* axm, int iax, const double* part_in,
-                          const T* dotm, int idot, const T* dotv, double* part_out) {
+__global__ void k_lb_dots(LbArgs a, const T* g, const T* Sm, const T* Ym, double* part) {
+  __shared__ double red[8][4 * (kMaxHistory + 1)];
+  const ChunkDev ch = a.chunks[blockIdx.x];
+  const LbfgsState S = a.st[ch.pair];
+  if (!S.active || S.hist_count == 0) return;
+  const PairDev pr = a.pairs[ch.pair];
+  const int RS = a.MH + 1, c = S.hist_count;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const T* yn = Ym + pr.off * RS + (long long)lb_age_slot(S, c - 1, RS) * pr.n;
+  for (int i = 0; i < c; ++i) {
+    const int sl = lb_age_slot(S, i, RS);
+    const T* sc = Sm + pr.off * RS + (long long)sl * pr.n;
+    const T* yc = Ym + pr.off * RS + (long long)sl * pr.n;
+    Accum<T> sg, yg, sy, yy;
+    for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
+      const long long li = ch.start + t;
+      const T sv = sc[li], yv = yc[li], gv = g[pr.off + li], ynv = yn[li];
+      sg.add(sv * gv);
+      yg.add(yv * gv);
+      sy.add(sv * ynv);
+      yy.add(yv * ynv);
+    }
+    const double v0 = warp_total(sg), v1 = warp_total(yg), v2 = warp_total(sy), v3 = warp_total(yy);
+    if (lane == 0) {
+      red[wid][4 * i + 0] = v0;
+      red[wid][4 * i + 1] = v1;
+      red[wid][4 * i + 2] = v2;
+      red[wid][4 * i + 3] = v3;
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < 4 * c; q += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < kChunkThreads / 32; ++w) t += red[w][q];
+    part[(size_t)blockIdx.x * 4 * RS + q] = t;
+  }
+}
+
+// Per pair: update S^T Y and Y^T Y for the newest pair, solve with R (FP64) and write the direction
+// coefficients by slot: d = -gamma g + sum_i cs_i s_i + cy_i y_i.
+__global__ void k_lb_compact(LbArgs a, const double* part) {
+  __shared__ double v[4 * (kMaxHistory + 1)];
+  const int k = blockIdx.x;
+  const LbfgsState S = a.st[k];
+  if (!S.active) return;
+  const PairDev pr = a.pairs[k];
+  const int RS = a.MH + 1, c = S.hist_count;
+  for (int q = threadIdx.x; q < 4 * c; q += blockDim.x) {
+    double t = 0.0;
+    for (int u = pr.cbeg; u < pr.cend; ++u) t += part[(size_t)u * 4 * RS + q];
+    v[q] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double* sy = a.sy + (size_t)k * RS * RS;    // sy[i * RS + j] = s_i^T y_j (slots)
+  double* yy = a.yy + (size_t)k * RS * RS;
+  double* cs = a.cs + (size_t)k * RS;
+  double* cy = a.cy + (size_t)k * RS;
+  for (int j = 0; j < RS; ++j) cs[j] = cy[j] = 0.0;
+  if (c == 0) return;
+  const int nw = lb_age_slot(S, c - 1, RS);
+  for (int i = 0; i < c; ++i) {
+    const int sl = lb_age_slot(S, i, RS);
+    sy[sl * RS + nw] = v[4 * i + 2];
+    yy[sl * RS + nw] = v[4 * i + 3];
+    yy[nw * RS + sl] = v[4 * i + 3];
+  }
+  double R[kMaxHistory][kMaxHistory], u[kMaxHistory], w[kMaxHistory], top[kMaxHistory];
+  for (int i = 0; i < c; ++i)
+    for (int j = 0; j < c; ++j)
+      R[i][j] = (j >= i) ? sy[lb_age_slot(S, i, RS) * RS + lb_age_slot(S, j, RS)] : 0.0;
+  const double gam = S.gamma;
+  // u = R^{-1} (S^T g)
+  for (int i = c - 1; i >= 0; --i) {
+    double t = v[4 * i + 0];
+    for (int j = i + 1; j < c; ++j) t -= R[i][j] * u[j];
+    u[i] = t / R[i][i];
+  }
+  // w = (D + gamma Y^T Y) u - gamma Y^T g
+  for (int i = 0; i < c; ++i) {
+    double t = R[i][i] * u[i] - gam * v[4 * i + 1];
+    for (int j = 0; j < c; ++j) t += gam * yy[lb_age_slot(S, i, RS) * RS + lb_age_slot(S, j, RS)] * u[j];
+    w[i] = t;
+  }
+  // top = R^{-T} w
+  for (int i = 0; i < c; ++i) {
+    double t = w[i];
+    for (int j = 0; j < i; ++j) t -= R[j][i] * top[j];
+    top[i] = t / R[i][i];
+  }
+  for (int i = 0; i < c; ++i) {
+    const int sl = lb_age_slot(S, i, RS);
+    cs[sl] = -top[i];
+    cy[sl] = gam * u[i];
+  }
+}
+
+// Pass B: d = -gamma g + sum_i cs_i s_i + cy_i y_i; partial g^T d.
+template <typename T>
+__global__ void k_lb_dir(LbArgs a, T* d, const T* g, const T* Sm, const T* Ym, double* part) {
   __shared__ double red[40];
+  __shared__ T cf[2 * (kMaxHistory + 1)];
+  __shared__ int sl[kMaxHistory + 1];
   const ChunkDev ch = a.chunks[blockIdx.x];
   const LbfgsState S = a.st[ch.pair];
   if (!S.active) return;
   const PairDev pr = a.pairs[ch.pair];
-  T coef = 0;
-  const T* axc = nullptr;
-  if ((mode == 1 || mode == 3) && iax < S.hist_count) {
-    double sum = 0.0;
-    for (int u = pr.cbeg; u < pr.cend; ++u) sum += part_in[u];
-    const double v = S.rho_hist[lb_slot(S, iax, a.MH)] * sum;
-    if (mode == 1) {
-      coef = (T)(-v);
-      if (blockIdx.x == pr.cbeg && threadIdx.x == 0) a.acoef[ch.pair * a.MH + iax] = v;
-    } else {
-      coef = (T)(a.acoef[ch.pair * a.MH + iax] - v);
-    }
-    axc = axm + pr.off * a.MH + (long long)lb_slot(S, iax, a.MH) * pr.n;
+  const int RS = a.MH + 1, c = S.hist_count;
+  if ((int)threadIdx.x < c) {
+    const int s_ = lb_age_slot(S, threadIdx.x, RS);
+    sl[threadIdx.x] = s_;
+    cf[2 * threadIdx.x] = (T)a.cs[(size_t)ch.pair * RS + s_];
+    cf[2 * threadIdx.x + 1] = (T)a.cy[(size_t)ch.pair * RS + s_];
   }
-  const T* dc = nullptr;
-  if (idot >= 0 && idot < S.hist_count) dc = dotm + pr.off * a.MH + (long long)lb_slot(S, idot, a.MH) * pr.n;
-  else if (idot == -2) dc = dotv + pr.off;
-  const T gam = (T)S.gamma;
+  __syncthreads();
+  const T mg = (T)(-S.gamma);
   Accum<T> acc;
   for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
     const long long li = ch.start + t, gi = pr.off + li;
-    T x;
-    if (mode == 0) x = src[gi];
-    else if (mode == 2) x = gam * X[gi];
-    else if (mode == 5) x = -src[gi];
-    else {
-      x = X[gi];
-      if (axc) x = fma(coef, axc[li], x);
+    const T gv = g[gi];
+    T x = mg * gv;
+    for (int i = 0; i < c; ++i) {
+      const long long col = pr.off * RS + (long long)sl[i] * pr.n + li;
+      x = fma(cf[2 * i], Sm[col], fma(cf[2 * i + 1], Ym[col], x));
     }
-    X[gi] = x;
-    if (dc) acc.add(dc[li] * x);
+    d[gi] = x;
+    acc.add(gv * x);
   }
   const double tot = block_total<kChunkThreads>(acc, red);
-  if (threadIdx.x == 0) part_out[blockIdx.x] = tot;
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
-// g^T d from the partials of the last two-loop launch; descent check (restart flag if >= 0)
+// g^T d from the partials of the direction pass; descent check (restart flag if >= 0)
 __global__ void k_lb_gtd(LbArgs a, const double* part) {
   const int k = blockIdx.x;
   LbfgsState& S = a.st[k];
@@ -173,8 +265,8 @@ __global__ void k_lb_accept(LbArgs a, T* x, T* g, const T* xt, const T* gt, T* S
   const LbfgsState S = a.st[ch.pair];
   if (!S.active) return;
   const PairDev pr = a.pairs[ch.pair];
-  T* sc = Sm + pr.off * a.MH + (long long)S.hist_head * pr.n;
-  T* yc = Ym + pr.off * a.MH + (long long)S.hist_head * pr.n;
+  T* sc = Sm + pr.off * (a.MH + 1) + (long long)S.hist_head * pr.n;
+  T* yc = Ym + pr.off * (a.MH + 1) + (long long)S.hist_head * pr.n;
   Accum<T> sy, yy, ss, gg;
   for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
     const long long li = ch.start + t, gi = pr.off + li;
@@ -211,9 +303,8 @@ __global__ void k_lb_post(LbArgs a, int maxit, int* flag) {
     for (int c = 0; c < 4; ++c) v[c] += a.cpart[(size_t)u * 4 + c];
   const double sy = v[0], yy = v[1], ss = v[2], gg = v[3];
   if (sy > 1e-12 * sqrt(ss) * sqrt(yy)) {
-    S.rho_hist[S.hist_head] = 1.0 / sy;
     S.gamma = sy / yy;
-    S.hist_head = (S.hist_head + 1) % a.MH;
+    S.hist_head = (S.hist_head + 1) % (a.MH + 1);
     S.hist_count = min(S.hist_count + 1, a.MH);
   }
   if (S.hist_count == 0) S.gamma = 1.0;
@@ -265,7 +356,7 @@ template <typename T>
 static bl_status lbfgs_impl(bl_problem* P, const std::vector<int>& mask_host, const bl_lbfgs_opts* o,
                             std::vector<bl_solve_info>& info) {
   const int K = P->K, MH = P->MH;
-  bl_status st = ensure_cpart(P, (size_t)P->n_chunks * 4);
+  bl_status st = ensure_cpart(P, (size_t)P->n_chunks * (4 * (MH + 1) + 1));
   if (st != BL_OK) return st;
   LbArgs a{};
   a.pairs = P->d_pairs;
@@ -273,7 +364,10 @@ static bl_status lbfgs_impl(bl_problem* P, const std::vector<int>& mask_host, co
   a.st = P->lst;
   a.MH = MH;
   a.cpart = P->cpart;
-  a.acoef = P->dY3;   // K x MH doubles of scratch
+  a.sy = P->lsy;
+  a.yy = P->lyy;
+  a.cs = P->lcs;
+  a.cy = P->lcy;
   const int* mask = P->d_active;
   int* smask = P->d_active + K;
   T* x = (T*)P->lx;
@@ -281,7 +375,6 @@ static bl_status lbfgs_impl(bl_problem* P, const std::vector<int>& mask_host, co
   T* d = (T*)P->ld;
   T* xt = (T*)P->lxt;
   T* gt = (T*)P->lgt;
-  T* q = (T*)P->lq;
   T* Sm = (T*)P->S;
   T* Ym = (T*)P->Yh;
   double* vals = P->vals;              // K x 3
@@ -308,36 +401,19 @@ static bl_status lbfgs_impl(bl_problem* P, const std::vector<int>& mask_host, co
   BL_CUDA_TRY(cudaStreamSynchronize(P->stream));
   int hist = 0;   // upper bound on any pair's history count
   for (int it = 0; it < o->max_iters && *P->h_flag > 0; ++it) {
-    // ---- two-loop recursion: q = g; newest to oldest ----
-    const int m = std::min(hist, MH);
+    // ---- direction d = -H g (compact representation) ----
     {
     ProfScope ps(P, BL_KC_LBFGS);
-    double* pb[2] = {P->cpart, P->cpart + P->n_chunks};   // ping-pong partial sums
-    int cur = 0;
-    k_lb_step<T><<<cg, ct, 0, P->stream>>>(a, q, g, 0, nullptr, 0, nullptr, Sm, m > 0 ? 0 : -1, nullptr, pb[cur]);
-    BL_LAUNCH_CHECK(P);
-    for (int i = 0; i < m; ++i) {
-      k_lb_step<T><<<cg, ct, 0, P->stream>>>(a, q, nullptr, 1, Ym, i, pb[cur], Sm, i + 1 < m ? i + 1 : -1,
-                                             nullptr, pb[cur ^ 1]);
+    if (hist > 0) {
+      k_lb_dots<T><<<cg, ct, 0, P->stream>>>(a, g, Sm, Ym, P->cpart);
       BL_LAUNCH_CHECK(P);
-      cur ^= 1;
     }
-    // q = gamma q; oldest to newest
-    k_lb_step<T><<<cg, ct, 0, P->stream>>>(a, q, nullptr, 2, nullptr, 0, nullptr, Ym, m > 0 ? m - 1 : -1, nullptr,
-                                           pb[cur ^ 1]);
+    k_lb_compact<<<K, 32, 0, P->stream>>>(a, P->cpart);
     BL_LAUNCH_CHECK(P);
-    cur ^= 1;
-    for (int i = m - 1; i >= 0; --i) {
-      k_lb_step<T><<<cg, ct, 0, P->stream>>>(a, q, nullptr, 3, Sm, i, pb[cur], Ym, i > 0 ? i - 1 : -1, nullptr,
-                                             pb[cur ^ 1]);
-      BL_LAUNCH_CHECK(P);
-      cur ^= 1;
-    }
-    // d = -q with g^T d
-    k_lb_step<T><<<cg, ct, 0, P->stream>>>(a, d, q, 5, nullptr, 0, nullptr, nullptr, -2, g, pb[cur ^ 1]);
+    double* pd = P->cpart + (size_t)P->n_chunks * 4 * (MH + 1);
+    k_lb_dir<T><<<cg, ct, 0, P->stream>>>(a, d, g, Sm, Ym, pd);
     BL_LAUNCH_CHECK(P);
-    cur ^= 1;
-    k_lb_gtd<<<K, 32, 0, P->stream>>>(a, pb[cur]);
+    k_lb_gtd<<<K, 32, 0, P->stream>>>(a, pd);
     BL_LAUNCH_CHECK(P);
     k_lb_restart<T><<<cg, ct, 0, P->stream>>>(a, d, g);
     BL_LAUNCH_CHECK(P);

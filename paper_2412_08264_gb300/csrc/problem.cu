@@ -60,17 +60,23 @@ std::vector<int> host_mask(const bl_problem* P, const int32_t* pairs, int32_t np
 }
 
 bl_status ensure_history(bl_problem* P, int m) {
-  if (m <= P->MH && P->S) return BL_OK;
+  if (m == P->MH && P->S) return BL_OK;
   if (P->S) {
     cudaStreamSynchronize(P->stream);
-    cudaFree(P->S);
-    cudaFree(P->Yh);
+    for (void* b : {(void*)P->S, (void*)P->Yh, (void*)P->lsy, (void*)P->lyy, (void*)P->lcs, (void*)P->lcy})
+      cudaFree(b);
     P->S = P->Yh = nullptr;
+    P->lsy = P->lyy = P->lcs = P->lcy = nullptr;
   }
   P->MH = m;
-  bl_status st = alloc_vec(P, &P->S, (size_t)P->n_tot * m);
-  if (st != BL_OK) return st;
-  return alloc_vec(P, &P->Yh, (size_t)P->n_tot * m);
+  const size_t rs = (size_t)m + 1;
+  bl_status st = alloc_vec(P, &P->S, (size_t)P->n_tot * rs);
+  if (st == BL_OK) st = alloc_vec(P, &P->Yh, (size_t)P->n_tot * rs);
+  if (st == BL_OK) st = dalloc((void**)&P->lsy, (size_t)P->K * rs * rs * sizeof(double));
+  if (st == BL_OK) st = dalloc((void**)&P->lyy, (size_t)P->K * rs * rs * sizeof(double));
+  if (st == BL_OK) st = dalloc((void**)&P->lcs, (size_t)P->K * rs * sizeof(double));
+  if (st == BL_OK) st = dalloc((void**)&P->lcy, (size_t)P->K * rs * sizeof(double));
+  return st;
 }
 
 }  // namespace
@@ -171,7 +177,8 @@ void bl_problem_destroy(bl_problem* P) {
                   P->taps_f, P->taps_d, P->ealpha, P->r, P->pv, P->q, P->w, P->g, P->tmp, P->U, P->C, P->Z,
                   P->V, P->W, P->Wt, P->HWt, P->st, P->c, P->zc, P->e, P->ztr, P->ztc, P->d_s, P->d_hasz,
                   P->d_active, P->d_cols, P->d_flag, P->dG, P->dT, P->dJ, P->dY, P->dY2, P->dY3, P->d_tk,
-                  P->lx, P->lg, P->ld, P->lxt, P->lgt, P->lq, P->S, P->Yh, P->lst, P->tpart, P->cpart, P->vals,
+                  P->lx, P->lg, P->ld, P->lxt, P->lgt, P->lq, P->S, P->Yh, P->lsy, P->lyy, P->lcs, P->lcy,
+                  P->lst, P->tpart, P->cpart, P->vals,
                   P->d_pix, P->d_zero, P->d_loop};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -432,7 +439,6 @@ bl_status bl_lower_solve(bl_problem* P, const int32_t* pairs, int32_t npairs, co
   if (o->max_iters < 0 || !(o->gtol >= 0.0) || !(o->armijo_slack >= 0.0))
     return fail(BL_EINVAL, "invalid L-BFGS options");
   if ((st = ensure_history(P, o->history)) != BL_OK) return st;
-  P->MH = o->history;
   if ((st = set_active_pairs(P, pairs, npairs)) != BL_OK) return st;
   if ((st = load_theta(P, theta)) != BL_OK) return st;
   if ((st = gather_packed(P, pairs, npairs, xhat, P->lx)) != BL_OK) return st;

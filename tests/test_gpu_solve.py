@@ -128,6 +128,29 @@ def test_lower_solve_first_order_condition():
             assert info[k]["status"] == 0
 
 
+def test_lower_solve_trajectory_fp64_matches_checker():
+    """A fixed number of L-BFGS iterations (history 4, so the (s, y) ring wraps several times)
+    from x = 0: the GPU's compact-form direction, Armijo backtracking and history updates follow
+    the checker's two-loop L-BFGS iterate for iterate."""
+    from oracle.lbfgs import lbfgs
+    wl = small_wl(sizes=((37, 45), (20, 26)), N=3, seed=21)
+    P, prob, dt = make(wl, "fp64")
+    th = wl.theta0
+    theta = torch.tensor(th, dtype=torch.float64, device=DEV)
+    for iters in (3, 40):
+        x = P.zeros()
+        info = P.lower_solve(theta, x, gtol=0.0, relative=False, max_iters=iters, history=4, max_backtrack=30,
+                             armijo_slack=0.0, allow_noconv=True)
+        xs = split(x, P.sizes)
+        for k, ll in enumerate(prob.lowers):
+            h, w = xs[k].shape
+            xr, out = lbfgs(lambda z: ll.value(z.reshape(h, w), th), lambda z: ll.grad(z.reshape(h, w), th).ravel(),
+                            np.zeros(h * w), gtol=0.0, m=4, maxit=iters, max_backtrack=30)
+            assert info[k]["iters"] == out["iters"] == iters
+            assert rel(xs[k], xr) < 1e-9, (iters, k, rel(xs[k], xr))
+            assert abs(info[k]["value"] - out["f"]) <= 1e-10 * abs(out["f"])
+
+
 def test_full_hypergradient_fp32():
     """Lower solve, Hessian solve and J w on the GPU (FP32) against the checker's reference."""
     wl = small_wl(sizes=((56, 56), (40, 72)), N=4, seed=11)
