@@ -118,6 +118,7 @@ struct bl_problem {
   cudaStream_t stream = nullptr;
   int64_t launches = 0;
   int n_tiles = 0, n_chunks = 0;
+  bool vec4 = false;                // every pair's n is a multiple of 4 (16-byte column starts)
 
   bl::PairDev* d_pairs = nullptr;
   bl::TileDev* d_tiles = nullptr;
@@ -244,5 +245,13 @@ bl_status reduce_chunk_partials(bl_problem* P, int ncomp, const int* mask, doubl
 bl_status reduce_tile_partials(bl_problem* P, int ncomp, int cols, const int* mask, double* out);
 // dot products per pair: out[k] = sum_i a_i b_i (FP64 accumulation).
 bl_status batched_dot(bl_problem* P, const void* a, const void* b, const int* mask, double* out);
+// Tall-skinny products (tsmm.cu).  ts_gram: out[k] (TM x TM, FP64) = A_k^T B_k over the colsA[k]
+// and colsB[k] leading columns (cmaxA, cmaxB: their maxima).  ts_gemm: O1_k = A_k M1_k (cols1[k]
+// columns), O2_k = A_k M2_k (optional); M: K x TM x TM FP64; O1 may alias A.
+bl_status ts_gram(bl_problem* P, const void* A, int multA, const int* colsA, int cmaxA, const void* B, int multB,
+                  const int* colsB, int cmaxB, const int* mask, double* out);
+bl_status ts_gemm(bl_problem* P, const void* A, int multA, const int* colsA, int cmaxA, const double* M1, void* O1,
+                  int mult1, const int* cols1, int cmax1, const double* M2, void* O2, int mult2, const int* cols2,
+                  int cmax2, const int* mask);
 
 }  // namespace bl

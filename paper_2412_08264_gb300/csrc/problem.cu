@@ -283,6 +283,8 @@ bl_status bl_problem_create(const bl_pair_desc* pairs, int32_t K, const bl_reg_d
   P->n_tot = off;
   P->n_tiles = (int)tiles.size();
   P->n_chunks = (int)chunks.size();
+  P->vec4 = true;
+  for (const auto& ph : P->ph) P->vec4 = P->vec4 && (ph.n % 4 == 0);
   P->s_k.assign(K, 0);
   P->kb_k.assign(K, 0);
   P->hz_k.assign(K, 0);

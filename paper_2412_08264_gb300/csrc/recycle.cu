@@ -2,7 +2,9 @@
 //
 // For every listed pair with W = [U^(i-1), V^(i-1)] (t = s + k columns):
 //   1. G = W^T W; W~ = W D Q Lambda^{-1/2} from the eigenpairs of the column-scaled Gram,
-//      dropping directions below a relative threshold (orthonormal basis of range(W)).
+//      dropping directions below a relative threshold (orthonormal basis of range(W)).  W~ is
+//      formed explicitly: projecting W^T H W with the coefficients instead would square their
+//      conditioning in the projected matrices.
 //   2. HW~ = H W~ (t' Hessian actions at the current point: the outer form, eq. (3.3)).
 //   3. T = W~^T H W~; for Ritz-GSV also J~ = J W~ (eq. (3.4)), for harmonic Ritz (HW~)^T HW~.
 //   4. Small FP64 problem on one CTA per pair:
@@ -19,161 +21,6 @@
 #include "device.cuh"
 
 namespace bl {
-
-constexpr int kGramRows = 32;   // FP32 sub-sum length before the compensated accumulation
-
-// Tall-skinny Gram partials: part[chunk][i * TM + j] = sum_{rows in chunk} A[row][i] B[row][j].
-// FP32 products summed over kGramRows rows, then accumulated as an FP32 (hi, lo) pair with
-// the error-free TwoSum; chunks are combined in FP64 by reduce_units.
-template <typename T>
-__global__ void __launch_bounds__(256) k_ts_gram(const PairDev* pairs, const ChunkDev* chunks, const T* A, int multA,
-                                                 const int* colsA, const T* B, int multB, const int* colsB,
-                                                 const int* mask, int TM, double* part) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const ChunkDev ch = chunks[blockIdx.x];
-  if (mask && !mask[ch.pair]) return;
-  const PairDev pr = pairs[ch.pair];
-  const int ta = colsA[ch.pair], tb = colsB[ch.pair];
-  if (ta == 0 || tb == 0) return;
-  T* As = reinterpret_cast<T*>(smem_raw);               // kGramRows x (TM + 1)
-  T* Bs = As + kGramRows * (TM + 1);
-  const int tid = threadIdx.x;
-  const int nti = (ta + 5) / 6, ntj = (tb + 5) / 6;
-  const bool act = tid < nti * ntj;
-  const int ti = act ? tid / ntj : 0, tj = act ? tid - (tid / ntj) * ntj : 0;
-  float hi[6][6], lo[6][6];
-#pragma unroll
-  for (int i = 0; i < 6; ++i)
-#pragma unroll
-    for (int j = 0; j < 6; ++j) hi[i][j] = lo[i][j] = 0.f;
-  const T* Ab = A + pr.off * multA;
-  const T* Bb = B + pr.off * multB;
-  for (int r0 = 0; r0 < ch.len; r0 += kGramRows) {
-    const int nr = min(kGramRows, ch.len - r0);
-    __syncthreads();
-    for (int idx = tid; idx < kGramRows * ta; idx += blockDim.x) {
-      const int c = idx / kGramRows, rr = idx - c * kGramRows;
-      As[rr * (TM + 1) + c] = rr < nr ? Ab[(long long)c * pr.n + ch.start + r0 + rr] : T(0);
-    }
-    for (int idx = tid; idx < kGramRows * tb; idx += blockDim.x) {
-      const int c = idx / kGramRows, rr = idx - c * kGramRows;
-      Bs[rr * (TM + 1) + c] = rr < nr ? Bb[(long long)c * pr.n + ch.start + r0 + rr] : T(0);
-    }
-    __syncthreads();
-    if (!act) continue;
-    float ps[6][6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-      for (int j = 0; j < 6; ++j) ps[i][j] = 0.f;
-    for (int rr = 0; rr < kGramRows; ++rr) {
-      float av[6], bv[6];
-#pragma unroll
-      for (int i = 0; i < 6; ++i) {
-        const int ci = 6 * ti + i, cj = 6 * tj + i;
-        av[i] = ci < ta ? (float)As[rr * (TM + 1) + ci] : 0.f;
-        bv[i] = cj < tb ? (float)Bs[rr * (TM + 1) + cj] : 0.f;
-      }
-#pragma unroll
-      for (int i = 0; i < 6; ++i)
-#pragma unroll
-        for (int j = 0; j < 6; ++j) ps[i][j] = fmaf(av[i], bv[j], ps[i][j]);
-    }
-#pragma unroll
-    for (int i = 0; i < 6; ++i)
-#pragma unroll
-      for (int j = 0; j < 6; ++j) {
-        // TwoSum(hi, ps): exact sum s + err
-        const float s = hi[i][j] + ps[i][j];
-        const float bb = s - hi[i][j];
-        const float err = (hi[i][j] - (s - bb)) + (ps[i][j] - bb);
-        hi[i][j] = s;
-        lo[i][j] += err;
-      }
-  }
-  if (!act) return;
-  double* out = part + (size_t)blockIdx.x * TM * TM;
-#pragma unroll
-  for (int i = 0; i < 6; ++i)
-#pragma unroll
-    for (int j = 0; j < 6; ++j) {
-      const int ci = 6 * ti + i, cj = 6 * tj + j;
-      if (ci < ta && cj < tb) out[ci * TM + cj] = (double)hi[i][j] + (double)lo[i][j];
-    }
-}
-
-// Double-precision variant for FP64 problems: plain FP64 accumulation.
-template <>
-__global__ void __launch_bounds__(256) k_ts_gram<double>(const PairDev* pairs, const ChunkDev* chunks, const double* A,
-                                                         int multA, const int* colsA, const double* B, int multB,
-                                                         const int* colsB, const int* mask, int TM, double* part) {
-  const ChunkDev ch = chunks[blockIdx.x];
-  if (mask && !mask[ch.pair]) return;
-  const PairDev pr = pairs[ch.pair];
-  const int ta = colsA[ch.pair], tb = colsB[ch.pair];
-  const double* Ab = A + pr.off * multA;
-  const double* Bb = B + pr.off * multB;
-  double* out = part + (size_t)blockIdx.x * TM * TM;
-  for (int e = threadIdx.x; e < ta * tb; e += blockDim.x) {
-    const int i = e / tb, j = e - (e / tb) * tb;
-    double s = 0.0;
-    for (int r = 0; r < ch.len; ++r)
-      s += Ab[(long long)i * pr.n + ch.start + r] * Bb[(long long)j * pr.n + ch.start + r];
-    out[i * TM + j] = s;
-  }
-}
-
-// out[row][j] = sum_l A[row][l] M[l][j]   (M: ta x tb, FP64, ld TM); in place allowed (out == A).
-template <typename T>
-__global__ void __launch_bounds__(256) k_ts_gemm(const PairDev* pairs, const ChunkDev* chunks, const T* A, int multA,
-                                                 const int* colsA, const double* M, int TM, T* out, int multO,
-                                                 const int* colsO, const int* mask) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const ChunkDev ch = chunks[blockIdx.x];
-  if (mask && !mask[ch.pair]) return;
-  const PairDev pr = pairs[ch.pair];
-  const int ta = colsA[ch.pair], tb = colsO[ch.pair];
-  if (tb == 0) return;
-  T* Ms = reinterpret_cast<T*>(smem_raw);        // ta x tb
-  T* As = Ms + TM * TM;                          // 64 rows x (ta + 1)
-  const double* Mk = M + (size_t)ch.pair * TM * TM;
-  for (int idx = threadIdx.x; idx < ta * tb; idx += blockDim.x) {
-    const int l = idx / tb, j = idx - (idx / tb) * tb;
-    Ms[l * tb + j] = (T)Mk[l * TM + j];
-  }
-  const T* Ab = A + pr.off * multA;
-  T* Ob = out + pr.off * multO;
-  const int ngrp = (tb + 23) / 24;
-  for (int r0 = 0; r0 < ch.len; r0 += 64) {
-    const int nr = min(64, ch.len - r0);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < 64 * ta; idx += blockDim.x) {
-      const int l = idx / 64, rr = idx - l * 64;
-      As[rr * (ta + 1) + l] = rr < nr ? Ab[(long long)l * pr.n + ch.start + r0 + rr] : T(0);
-    }
-    __syncthreads();
-    for (int job = threadIdx.x; job < 64 * ngrp; job += blockDim.x) {
-      const int rr = job & 63, grp = job >> 6;
-      if (rr >= nr) continue;
-      T acc[24];
-#pragma unroll
-      for (int j = 0; j < 24; ++j) acc[j] = T(0);
-      for (int l = 0; l < ta; ++l) {
-        const T av = As[rr * (ta + 1) + l];
-#pragma unroll
-        for (int j = 0; j < 24; ++j) {
-          const int cj = grp * 24 + j;
-          if (cj < tb) acc[j] = fma(av, Ms[l * tb + cj], acc[j]);
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < 24; ++j) {
-        const int cj = grp * 24 + j;
-        if (cj < tb) Ob[(long long)cj * pr.n + ch.start + r0 + rr] = acc[j];
-      }
-    }
-  }
-}
 
 // ---------------------------------------------------------------------------------------------
 // Small dense FP64 linear algebra, one CTA per pair.
@@ -327,7 +174,8 @@ struct DenseArgs {
   double* G;     // K x TM x TM: W^T W   -> scratch
   double* T;     // K x TM x TM: W~^T H W~
   double* GH;    // K x TM x TM: (HW~)^T HW~
-  const double* J;  // K x TM x p: J W~ ([k][col][m])
+  const double* J;  // K x jcols x p: J W~ ([k][col][m])
+  int jcols;
   double* Y;     // K x TM x TM: coefficient outputs
   double* Y2;    // K x TM x TM
   double* scratch;  // K x 4 x TM x TM
@@ -472,7 +320,7 @@ __global__ void k_dense_select(DenseArgs a) {
     return;
   }
   // RGSV: F = J~^T J~ (t x t) into S2, M = T^{-1} F T^{-1}
-  const double* J = a.J + (size_t)k * TM * a.p;
+  const double* J = a.J + (size_t)k * a.jcols * a.p;
   for (int idx = threadIdx.x; idx < t * t; idx += blockDim.x) {
     const int i = idx / t, j = idx - (idx / t) * t;
     if (j < i) continue;
@@ -558,36 +406,6 @@ __global__ void k_copy_ztc(const int* mask, const int* scols, const double* G, i
 }
 
 template <typename T>
-static bl_status gram(bl_problem* P, const void* A, int multA, const int* colsA, const void* B, int multB,
-                      const int* colsB, const int* mask, double* out) {
-  const int TM = P->TM;
-  bl_status st = ensure_cpart(P, (size_t)P->n_chunks * TM * TM);
-  if (st != BL_OK) return st;
-  // entries of pairs with fewer columns than TM stay unwritten: clear the partials first
-  ProfScope ps(P, BL_KC_GRAM);
-  BL_CUDA_TRY(cudaMemsetAsync(P->cpart, 0, (size_t)P->n_chunks * TM * TM * sizeof(double), P->stream));
-  const size_t sm = 2 * (size_t)kGramRows * (TM + 1) * sizeof(T);
-  BL_CUDA_TRY(cudaFuncSetAttribute(k_ts_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_ts_gram<T><<<P->n_chunks, 256, sm, P->stream>>>(P->d_pairs, P->d_chunks, (const T*)A, multA, colsA,
-                                                    (const T*)B, multB, colsB, mask, TM, P->cpart);
-  BL_LAUNCH_CHECK(P);
-  return reduce_units(P, P->cpart, TM * TM, 1, false, mask, nullptr, out);
-}
-
-template <typename T>
-static bl_status gemm(bl_problem* P, const void* A, int multA, const int* colsA, const double* M, void* out,
-                      int multO, const int* colsO, const int* mask) {
-  const int TM = P->TM;
-  const size_t sm = ((size_t)TM * TM + 64 * (TM + 1)) * sizeof(T);
-  ProfScope ps(P, BL_KC_GEMM);
-  BL_CUDA_TRY(cudaFuncSetAttribute(k_ts_gemm<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_ts_gemm<T><<<P->n_chunks, 256, sm, P->stream>>>(P->d_pairs, P->d_chunks, (const T*)A, multA, colsA, M, TM,
-                                                    (T*)out, multO, colsO, mask);
-  BL_LAUNCH_CHECK(P);
-  return BL_OK;
-}
-
-template <typename T>
 static bl_status refresh_impl(bl_problem* P, const std::vector<int>& mask_host, const bl_recycle_opts* o) {
   const int K = P->K, TM = P->TM;
   std::vector<int> msk(K, 0), tcols(K, 0);
@@ -619,6 +437,9 @@ static bl_status refresh_impl(bl_problem* P, const std::vector<int>& mask_host, 
       BL_CUDA_TRY(cudaMemcpyAsync(Wk + (size_t)P->s_k[k] * ph.n * P->esz, (const char*)P->V + ph.off * P->KMAX * P->esz,
                                   (size_t)P->kb_k[k] * ph.n * P->esz, cudaMemcpyDeviceToDevice, P->stream));
   }
+  int tmax = 0;
+  for (int k = 0; k < K; ++k) tmax = std::max(tmax, tcols[k]);
+  const int smax = std::min(o->s, P->SMAX);
   DenseArgs da{};
   da.TM = TM;
   da.p = P->p;
@@ -626,6 +447,7 @@ static bl_status refresh_impl(bl_problem* P, const std::vector<int>& mask_host, 
   da.T = P->dT;
   da.GH = P->dT + (size_t)K * TM * TM;
   da.J = P->dJ;
+  da.jcols = tmax;
   da.Y = P->dY;
   da.Y2 = P->dY2;
   da.scratch = P->dY3;
@@ -638,30 +460,30 @@ static bl_status refresh_impl(bl_problem* P, const std::vector<int>& mask_host, 
   da.s = o->s;
   da.drop = P->prec == BL_FP32 ? 1e-6 : 1e-12;
   const size_t dsm = (2 * (size_t)TM * TM + 4 * TM + 8) * sizeof(double) + TM * sizeof(int) + 64;
-  BL_CUDA_TRY(cudaFuncSetAttribute(k_dense_orth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
-  BL_CUDA_TRY(cudaFuncSetAttribute(k_dense_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+  if (!P->capturing) {
+    BL_CUDA_TRY(cudaFuncSetAttribute(k_dense_orth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+    BL_CUDA_TRY(cudaFuncSetAttribute(k_dense_select, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+  }
 
   // 1. orthonormal basis W~ = W B1
-  bl_status st = gram<T>(P, P->W, TM, d_t, P->W, TM, d_t, d_mask, P->dG);
+  bl_status st = ts_gram(P, P->W, TM, d_t, tmax, P->W, TM, d_t, tmax, d_mask, P->dG);
   if (st != BL_OK) return st;
   {
     ProfScope ps(P, BL_KC_DENSE);
     k_dense_orth<<<K, 256, dsm, P->stream>>>(da, d_t);
     BL_LAUNCH_CHECK(P);
   }
-  st = gemm<T>(P, P->W, TM, d_t, P->dY, P->Wt, TM, d_tk, d_mask);
+  st = ts_gemm(P, P->W, TM, d_t, tmax, P->dY, P->Wt, TM, d_tk, tmax, nullptr, nullptr, 0, nullptr, 0, d_mask);
   if (st != BL_OK) return st;
   // 2. H W~
   BL_CUDA_TRY(cudaMemcpyAsync(P->d_cols, d_tk, K * sizeof(int), cudaMemcpyDeviceToDevice, P->stream));
-  int tmax = 0;
-  for (int k = 0; k < K; ++k) tmax = std::max(tmax, tcols[k]);
   st = launch_hvp(P, P->Wt, P->HWt, TM, tmax, d_mask, nullptr, nullptr);
   if (st != BL_OK) return st;
   // 3. projected matrices
-  st = gram<T>(P, P->Wt, TM, d_tk, P->HWt, TM, d_tk, d_mask, P->dT);
+  st = ts_gram(P, P->Wt, TM, d_tk, tmax, P->HWt, TM, d_tk, tmax, d_mask, P->dT);
   if (st != BL_OK) return st;
   if (o->kind == BL_RECYCLE_HRITZ) {
-    st = gram<T>(P, P->HWt, TM, d_tk, P->HWt, TM, d_tk, d_mask, P->dT + (size_t)K * TM * TM);
+    st = ts_gram(P, P->HWt, TM, d_tk, tmax, P->HWt, TM, d_tk, tmax, d_mask, P->dT + (size_t)K * TM * TM);
     if (st != BL_OK) return st;
   }
   if (o->kind == BL_RECYCLE_RGSV) {
@@ -674,31 +496,31 @@ static bl_status refresh_impl(bl_problem* P, const std::vector<int>& mask_host, 
     k_dense_select<<<K, 256, dsm, P->stream>>>(da);
     BL_LAUNCH_CHECK(P);
   }
-  // 5. U~ = W~ Y, C~ = HW~ Y, Z = W~ Y2
-  st = gemm<T>(P, P->Wt, TM, d_tk, P->dY, P->U, P->SMAX, d_sn, d_mask);
+  // 5. U~ = W~ Y and Z = W~ Y2 in one pass over W~, C~ = HW~ Y
+  const bool rgsv = o->kind == BL_RECYCLE_RGSV;
+  st = ts_gemm(P, P->Wt, TM, d_tk, tmax, P->dY, P->U, P->SMAX, d_sn, smax, rgsv ? P->dY2 : nullptr,
+               rgsv ? P->Z : nullptr, P->SMAX, d_sn, smax, d_mask);
   if (st != BL_OK) return st;
-  st = gemm<T>(P, P->HWt, TM, d_tk, P->dY, P->C, P->SMAX, d_sn, d_mask);
+  st = ts_gemm(P, P->HWt, TM, d_tk, tmax, P->dY, P->C, P->SMAX, d_sn, smax, nullptr, nullptr, 0, nullptr, 0, d_mask);
   if (st != BL_OK) return st;
-  if (o->kind == BL_RECYCLE_RGSV) {
-    st = gemm<T>(P, P->Wt, TM, d_tk, P->dY2, P->Z, P->SMAX, d_sn, d_mask);
-    if (st != BL_OK) return st;
-  }
   // CholeskyQR2 of C~, applied to U~ as well
   for (int rep = 0; rep < 2; ++rep) {
-    st = gram<T>(P, P->C, P->SMAX, d_sn, P->C, P->SMAX, d_sn, d_mask, P->dG);
+    st = ts_gram(P, P->C, P->SMAX, d_sn, smax, P->C, P->SMAX, d_sn, smax, d_mask, P->dG);
     if (st != BL_OK) return st;
     {
       ProfScope ps(P, BL_KC_DENSE);
       k_dense_cholinv<<<K, 128, 0, P->stream>>>(da, d_sn, P->dG, P->dY);
       BL_LAUNCH_CHECK(P);
     }
-    st = gemm<T>(P, P->C, P->SMAX, d_sn, P->dY, P->C, P->SMAX, d_sn, d_mask);
+    st = ts_gemm(P, P->C, P->SMAX, d_sn, smax, P->dY, P->C, P->SMAX, d_sn, smax, nullptr, nullptr, 0, nullptr, 0,
+                 d_mask);
     if (st != BL_OK) return st;
-    st = gemm<T>(P, P->U, P->SMAX, d_sn, P->dY, P->U, P->SMAX, d_sn, d_mask);
+    st = ts_gemm(P, P->U, P->SMAX, d_sn, smax, P->dY, P->U, P->SMAX, d_sn, smax, nullptr, nullptr, 0, nullptr, 0,
+                 d_mask);
     if (st != BL_OK) return st;
   }
-  if (o->kind == BL_RECYCLE_RGSV) {
-    st = gram<T>(P, P->Z, P->SMAX, d_sn, P->C, P->SMAX, d_sn, d_mask, P->dG);
+  if (rgsv) {
+    st = ts_gram(P, P->Z, P->SMAX, d_sn, smax, P->C, P->SMAX, d_sn, smax, d_mask, P->dG);
     if (st != BL_OK) return st;
     k_copy_ztc<<<K, 128, 0, P->stream>>>(d_mask, d_sn, P->dG, TM, P->SMAX, P->ztc, K);
     BL_LAUNCH_CHECK(P);

@@ -83,9 +83,12 @@ def test_recycled_sequence_fp64_matches_checker():
         th = th - 0.05 * rng.standard_normal(th.shape) * 0.1
 
 
-def test_refresh_invariants_fp32():
-    """After bl_ritz_update: C = H U and C^T C = I on the exported recycle space (Section 2.2.2)."""
-    wl = small_wl(sizes=((64, 64), (40, 90)), N=4, seed=7)
+@pytest.mark.parametrize("sizes", [((64, 64), (40, 90)), ((37, 45), (100, 123))], ids=["aligned", "ragged"])
+def test_refresh_invariants_fp32(sizes):
+    """After bl_ritz_update: C = H U and C^T C = I on the exported recycle space (Section 2.2.2).
+    "aligned": every image a multiple of 4 pixels (16-byte staging of the tall-skinny kernels);
+    "ragged": odd sizes and an image spanning several 4096-pixel chunks with a short tail."""
+    wl = small_wl(sizes=sizes, N=4, seed=7)
     P, prob, dt = make(wl, "fp32", max_recycle=8, max_basis=60)
     th = r32(wl.theta0)
     xs = [r32(x) for x in lower_points(prob, th, gtol=1e-8)]
