@@ -30,7 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 S_RECYCLE = 16
-MAX_BASIS = 64
+MAX_BASIS = 32
 RTOL = 1e-4            # residual stopping tolerance (relative to ||g||)
 LOWER_GTOL = 1e-5      # lower-level gradient tolerance (relative to ||grad Phi(0)||)
 ADAM_LR = 1e-2
@@ -126,7 +126,7 @@ def gpu_arm(args, rank, world, dist):
     strategy = parse(args.strategy)
 
     def run(strat, steps, warmup, e2e=False, validate=False, profile_range=False, prof_steps=0):
-        P = api.from_workload(wl, y, xs, max_recycle=S_RECYCLE, max_basis=MAX_BASIS)
+        P = api.from_workload(wl, y, xs, max_recycle=S_RECYCLE, max_basis=args.max_basis)
         y_d = torch.empty_like(y)
         xs_d = torch.empty_like(xs)
         theta = wl.theta0.copy()
@@ -289,6 +289,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--strategy", default="RGen-L(R)")
+    ap.add_argument("--max-basis", type=int, default=MAX_BASIS,
+                    help="Krylov basis vectors kept per pair for the next refresh")
     ap.add_argument("--no-compare-cg", dest="compare_cg", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
@@ -358,7 +360,7 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"batch64_foe_n16f5: {K} pairs, sides 128-512, {n_pix} px, 16 5x5 filters, "
                                f"9x9 blur, p={wl.n_params}",
-                   "strategy": out["strategy"].acronym(), "recycle_dim": S_RECYCLE, "max_basis": MAX_BASIS,
+                   "strategy": out["strategy"].acronym(), "recycle_dim": S_RECYCLE, "max_basis": args.max_basis,
                    "stop": f"residual rtol {RTOL}", "lower_gtol_rel": LOWER_GTOL, "outer": "Adam lr 1e-2",
                    "l2": "inputs larger than L2 (batch working set > 1 GB), no flush"},
         "hg_rel_err_max": rec.get("hg_err_max"), "hg_rel_err_mean_grad": rec.get("hg_err_mean_grad"),

@@ -1,8 +1,9 @@
 // Recycle-space refresh (Section 3): Ritz, harmonic Ritz and Ritz generalized singular vectors.
 //
 // For every listed pair with W = [U^(i-1), V^(i-1)] (t = s + k columns):
-//   1. G = W^T W; W~ = W D Q Lambda^{-1/2} from the eigenpairs of the column-scaled Gram,
-//      dropping directions below a relative threshold (orthonormal basis of range(W)).  W~ is
+//   1. G = W^T W; W~ = W D P R^{-1} from the pivoted Cholesky factor of the column-scaled Gram,
+//      leaving out columns within a relative threshold of the span of those kept (an
+//      orthonormal basis of the numerical range of W).  W~ is
 //      formed explicitly: projecting W^T H W with the coefficients instead would square their
 //      conditioning in the projected matrices.
 //   2. HW~ = H W~ (t' Hessian actions at the current point: the outer form, eq. (3.3)).
@@ -51,7 +52,9 @@ __device__ void dev_jacobi(double* A, double* V, int n, double* w, double* cs, i
     ld = warp_sum(ld);
     if ((tid & 31) == 0) { atomicAdd(&offs, lo); atomicAdd(&dias, ld); }
     __syncthreads();
-    const bool done = !(offs > 1e-30 * dias) || offs == 0.0;
+    // converged when the off-diagonal mass is below (1e-12)^2 of the diagonal's: a few ulps of
+    // FP64 per entry for t <= 96 (a stricter bound is never reached through rounding)
+    const bool done = !(offs > 1e-24 * dias) || offs == 0.0;
     __syncthreads();
     if (done) break;
     for (int rnd = 0; rnd < m - 1; ++rnd) {
@@ -85,9 +88,12 @@ __device__ void dev_jacobi(double* A, double* V, int n, double* w, double* cs, i
         A[q * n + j] = s * ap + c * aq;
       }
       __syncthreads();
-      // columns: A <- A J, V <- V J
-      for (int idx = tid; idx < (m / 2) * n; idx += nt) {
-        const int i = idx / n, j = idx - (idx / n) * n;
+      // columns: A <- A J, V <- V J.  Consecutive threads take consecutive rotation pairs of one
+      // row j, so a warp touches one row at scattered columns (a column walk with stride n
+      // would put every lane of the warp in the same shared-memory bank).
+      const int hp = m / 2;
+      for (int idx = tid; idx < hp * n; idx += nt) {
+        const int j = idx / hp, i = idx - (idx / hp) * hp;
         const int p = (int)cs[4 * i + 2], q = (int)cs[4 * i + 3];
         if (q >= n) continue;
         const double c = cs[4 * i], s = cs[4 * i + 1];
@@ -183,25 +189,29 @@ struct DenseArgs {
   int* snew;     // selected size per pair (out)
   const int* mask;
   int kind, size, side, s;
-  double drop;   // relative eigenvalue threshold of the orthonormalisation
+  double drop;   // relative pivot threshold of the orthonormalisation
 };
 
-// 1. G (t x t) -> B1 (t x t'): orthonormal-basis coefficients
+// 1. G (t x t) -> B1 (t x t'): orthonormal-basis coefficients.  Pivoted Cholesky of the
+// column-scaled Gram D G D = P R^T R P^T, stopped when the largest remaining pivot falls below
+// `drop` (the columns left out lie within sqrt(drop) of the span of those kept); then
+// B1 = D P R^{-1}, so W~ = W B1 has W~^T W~ = I over the kept columns and spans them.
 __global__ void k_dense_orth(DenseArgs a, const int* tcols) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int k = blockIdx.x;
   if (!a.mask[k]) return;
   const int t = tcols[k], TM = a.TM;
-  double* As = reinterpret_cast<double*>(smem_raw);
-  double* Vs = As + TM * TM;
-  double* w = Vs + TM * TM;
-  double* dsc = w + TM;
-  double* cs = dsc + TM;                  // 4 * TM / 2
-  int* perm = reinterpret_cast<int*>(cs + 2 * TM + 4);
+  double* As = reinterpret_cast<double*>(smem_raw);   // t x t scaled Gram, updated in place
+  double* Rs = As + TM * TM;                          // t' x t' factor (row j: R[j][*], kept order)
+  double* dsc = Rs + TM * TM;
+  double* dres = dsc + TM;                            // remaining pivots
+  int* piv = reinterpret_cast<int*>(dres + TM);
+  __shared__ int s_stop, s_tk;
   const double* G = a.G + (size_t)k * TM * TM;
   for (int i = threadIdx.x; i < t; i += blockDim.x) {
     const double d = G[i * TM + i];
     dsc[i] = d > 0.0 ? 1.0 / sqrt(d) : 0.0;
+    piv[i] = i;
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < t * t; idx += blockDim.x) {
@@ -209,22 +219,58 @@ __global__ void k_dense_orth(DenseArgs a, const int* tcols) {
     As[idx] = 0.5 * (G[i * TM + j] + G[j * TM + i]) * dsc[i] * dsc[j];
   }
   __syncthreads();
-  dev_jacobi(As, Vs, t, w, cs, perm);
-  __shared__ int keep0, nkeep;
-  if (threadIdx.x == 0) {
-    const double wmax = t > 0 ? w[t - 1] : 0.0;
-    int k0 = 0;
-    while (k0 < t && !(w[k0] > a.drop * wmax)) ++k0;
-    keep0 = k0;
-    nkeep = t - k0;
-    a.tk[k] = t - k0;
-  }
+  for (int i = threadIdx.x; i < t; i += blockDim.x) dres[i] = As[i * t + i];
+  if (threadIdx.x == 0) s_tk = t;
   __syncthreads();
+  for (int j = 0; j < t; ++j) {
+    if (threadIdx.x == 0) {
+      int p = j;
+      for (int i = j + 1; i < t; ++i)
+        if (dres[piv[i]] > dres[piv[p]]) p = i;
+      s_stop = !(dres[piv[p]] > a.drop);   // unit diagonal: the threshold is relative
+      if (!s_stop) {
+        const int tmp = piv[j];
+        piv[j] = piv[p];
+        piv[p] = tmp;
+      } else {
+        s_tk = j;
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int pj = piv[j];
+    const double rjj = sqrt(dres[pj]);
+    // row j of R over the remaining columns (kept order), from the updated Schur complement
+    for (int i = j + threadIdx.x; i < t; i += blockDim.x) {
+      const int pi = piv[i];
+      Rs[j * TM + i] = (i == j) ? rjj : As[pj * t + pi] / rjj;
+    }
+    __syncthreads();
+    // trailing update A[pi][pl] -= R[j][i] R[j][l], i, l > j; remaining pivots
+    const int m = t - j - 1;
+    for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+      const int ii = j + 1 + idx / m, ll = j + 1 + idx % m;
+      As[piv[ii] * t + piv[ll]] -= Rs[j * TM + ii] * Rs[j * TM + ll];
+    }
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < t; i += blockDim.x) dres[piv[i]] = As[piv[i] * t + piv[i]];
+    __syncthreads();
+  }
+  const int tk = s_tk;
+  if (threadIdx.x == 0) a.tk[k] = tk;
+  // B1 = D P R^{-1}: column c solves R x = e_c (upper triangular), row piv[i] of B1 gets x_i
   double* Y = a.Y + (size_t)k * TM * TM;   // t x t'
-  for (int idx = threadIdx.x; idx < t * nkeep; idx += blockDim.x) {
-    const int i = idx / nkeep, j = idx - (idx / nkeep) * nkeep;
-    const int ev = perm[keep0 + j];
-    Y[i * TM + j] = dsc[i] * Vs[i * t + ev] / sqrt(w[keep0 + j]);
+  for (int idx = threadIdx.x; idx < t * tk; idx += blockDim.x) Y[(idx / tk) * TM + idx % tk] = 0.0;
+  __syncthreads();
+  for (int c = threadIdx.x; c < tk; c += blockDim.x) {
+    double x[kMaxTM];
+    for (int i = c + 1; i < tk; ++i) x[i] = 0.0;
+    for (int i = c; i >= 0; --i) {
+      double v = (i == c) ? 1.0 : 0.0;
+      for (int l = i + 1; l <= c; ++l) v -= Rs[i * TM + l] * x[l];
+      x[i] = v / Rs[i * TM + i];
+    }
+    for (int i = 0; i <= c; ++i) Y[piv[i] * TM + c] = dsc[piv[i]] * x[i];
   }
 }
 
