@@ -92,11 +92,16 @@ typedef struct {
                             values of Phi cannot resolve decreases below that level */
 } bl_lbfgs_opts;
 
-typedef enum { BL_SOLVE_CG = 0, BL_SOLVE_RCG = 1 } bl_solve_method;
+/* CG / recycled CG (augmented CG on P H P, P = I - C C^T: valid for SPD Hessians) and MINRES /
+   recycled MINRES (Algorithm 3 with the recurrences of Appendix A: valid for symmetric indefinite
+   Hessians, e.g. the non-convex phi = log(1 + s^2) of Section 5.2).  Both store the basis they
+   build (normalised CG residuals / Lanczos vectors) for bl_ritz_update. */
+typedef enum { BL_SOLVE_CG = 0, BL_SOLVE_RCG = 1, BL_SOLVE_MINRES = 2, BL_SOLVE_RMINRES = 3 } bl_solve_method;
 typedef enum { BL_STOP_RESID = 0, BL_STOP_NSC = 1 } bl_stop_rule;
 
 typedef struct {
-  int32_t method;        /* BL_SOLVE_CG ignores the recycle space; BL_SOLVE_RCG uses it (if any) */
+  int32_t method;        /* BL_SOLVE_CG / BL_SOLVE_MINRES ignore the recycle space; BL_SOLVE_RCG /
+                            BL_SOLVE_RMINRES use it (if any) */
   int32_t stop;          /* BL_STOP_RESID: ||r|| < tol * scale;
                             BL_STOP_NSC: ||Z^T r|| < tol * scale (eq. (4.2)); falls back to the
                             residual rule for a pair without a Ritz-GSV recycle space */
@@ -104,7 +109,8 @@ typedef struct {
   int32_t relative;      /* RESID: scale = ||g_k|| if non-zero, else 1.
                             NSC:   scale = nsc_scale[k] from bl_hessian_solve, else 1. */
   int32_t maxit;
-  int32_t store_basis;   /* keep normalised residuals as V for the next bl_ritz_update */
+  int32_t store_basis;   /* keep the basis (CG: normalised residuals; MINRES: Lanczos vectors) as V
+                            for the next bl_ritz_update */
   int32_t warm_start;    /* non-zero: w (in) is the initial guess; zero: start from 0 */
   int32_t graph;         /* non-zero: run the iteration loop as one CUDA-graph launch (a WHILE node whose
                             condition is set on the device), without host round trips; the stream path

@@ -18,7 +18,7 @@ STATUS_NAMES = {0: "BL_OK", 1: "BL_EINVAL", 2: "BL_ENOMEM", 3: "BL_ECUDA", 4: "B
 BL_REG_TV, BL_REG_FOE = 0, 1
 BL_PHI = {"charbonnier": 0, "sq": 1, "log1p": 2}
 BL_FP32, BL_FP64 = 0, 1
-BL_SOLVE_CG, BL_SOLVE_RCG = 0, 1
+BL_SOLVE_CG, BL_SOLVE_RCG, BL_SOLVE_MINRES, BL_SOLVE_RMINRES = 0, 1, 2, 3
 BL_STOP_RESID, BL_STOP_NSC = 0, 1
 BL_RECYCLE = {"ritz": 0, "hritz": 1, "rgsv": 2}
 BL_SIZE = {"S": 0, "L": 1, "M": 2}

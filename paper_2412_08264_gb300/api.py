@@ -139,12 +139,20 @@ class Problem:
     def hessian_solve(self, w: torch.Tensor, g: Optional[torch.Tensor] = None, pairs=None, recycle: bool = True,
                       nsc: bool = False, tol: float = 1e-4, relative: bool = True, maxit: int = 2000,
                       store_basis: bool = True, warm_start: bool = True, nsc_scale=None, allow_noconv=False,
-                      graph: bool = True):
+                      graph: bool = True, method: str = "cg"):
+        """method "cg": (recycled) CG, SPD Hessians; "minres": (recycled) MINRES (Algorithm 3),
+        symmetric indefinite Hessians."""
         pa, n, idx = self._pairs(pairs)
         self._check_images(w, idx)
         if g is not None:
             self._check_images(g, idx)
-        o = L.KrylovOpts(L.BL_SOLVE_RCG if recycle else L.BL_SOLVE_CG, L.BL_STOP_NSC if nsc else L.BL_STOP_RESID,
+        if method not in ("cg", "minres"):
+            raise ValueError(f"unknown Krylov method {method!r}")
+        if method == "cg":
+            meth = L.BL_SOLVE_RCG if recycle else L.BL_SOLVE_CG
+        else:
+            meth = L.BL_SOLVE_RMINRES if recycle else L.BL_SOLVE_MINRES
+        o = L.KrylovOpts(meth, L.BL_STOP_NSC if nsc else L.BL_STOP_RESID,
                          float(tol), 1 if relative else 0, int(maxit), 1 if store_basis else 0,
                          1 if warm_start else 0, 1 if graph else 0)
         sc = None

@@ -64,6 +64,9 @@ struct ChunkDev { int pair; long long start; int len; };
 // Per-pair scalar state of a Krylov solve (FP64 recurrences).
 struct SolveState {
   double rho, rho_new, alpha, beta, pq, est, tol, gnorm2;
+  // MINRES: Lanczos beta_k, zeta_k, the last two Givens rotations, and the step coefficients
+  // (gamma_k, delta_k, 1 / eps~_k, c_k zeta_{k-1}, 1 / beta_{k+1}) handed to the update pass
+  double beta_l, zeta, cm1, sm1, cm2, sm2, gam, del, inv_et, coef, inv_bn;
   int active, iters, status, maxit;
 };
 
@@ -83,10 +86,11 @@ struct ProfEvent {
 // Cached CUDA graph of the recycled-CG loop (a WHILE node around one iteration).
 struct KrylovGraphKey {
   bool fused;
-  int store, nsc;
+  int store, nsc, minres;
   const void *tpart, *cpart, *V;
   bool operator==(const KrylovGraphKey& o) const {
-    return fused == o.fused && store == o.store && nsc == o.nsc && tpart == o.tpart && cpart == o.cpart && V == o.V;
+    return fused == o.fused && store == o.store && nsc == o.nsc && minres == o.minres && tpart == o.tpart &&
+           cpart == o.cpart && V == o.V;
   }
 };
 struct KrylovGraph {
@@ -134,6 +138,10 @@ struct bl_problem {
 
   // Krylov vectors and recycle state
   void *r = nullptr, *pv = nullptr, *q = nullptr, *w = nullptr, *g = nullptr, *tmp = nullptr;
+  // MINRES vectors (v_{k-1}, vt_{k-1}, vt_{k-2}) and s-vectors (beta~_{k-1,k-2}, Z^T Hvt_{k-1,k-2}),
+  // allocated on the first MINRES solve
+  void *mv_prev = nullptr, *my1 = nullptr, *my2 = nullptr;
+  double* mrs = nullptr;
   void *U = nullptr, *C = nullptr, *Z = nullptr, *V = nullptr;
   void *W = nullptr, *Wt = nullptr, *HWt = nullptr;
   bl::SolveState* st = nullptr;

@@ -10,6 +10,16 @@
 // over to CG).  The hypergradient-error estimate of eq. (4.2), ||Z^T r||, is formed from the
 // updated residual in the same pass that updates it.
 //
+// Recycled MINRES (Algorithm 3, for symmetric indefinite Hessians) shares the initial projection
+// and runs Lanczos on P H P from v_1 = r_0 / beta_1, the QR factorisation of the tridiagonal by
+// Givens rotations (c_k, s_k) and zeta_k = -s_k zeta_{k-1} (|zeta_k| is the residual norm).  The
+// direction vt_k = (v_k - gamma_k vt_{k-2} - delta_k vt_{k-1}) / eps~_k updates w by
+// c_k zeta_{k-1} vt_k; its recycle-space part bt_k = U beta~_k, with the s coefficients beta~_k
+// following the same recurrence driven by C^T H v_k, is subtracted through z (the minus sign of the
+// reading of Algorithm 3).  The explicit residual of Appendix A enters the hypergradient-error rule
+// only through Z^T res, carried by the s-dimensional images of its recurrence, Z^T Hvt_k and
+// Z^T C beta~_k.
+//
 // All pairs advance together: vectors are batched over pairs, every per-pair scalar (rho, alpha,
 // beta, the s-vectors c, z, Z^T r) lives on the device in FP64, and each kernel skips the pairs
 // whose `active` flag is cleared (converged, iteration cap or breakdown).  The Hessian action
@@ -36,6 +46,7 @@ struct KrylovArgs {
   double* cpart;
   const double* tpart;
   int n_tiles, n_chunks;
+  double *b1, *b2, *h1, *h2;   // MINRES: beta~_{k-1}, beta~_{k-2}, Z^T Hvt_{k-1}, Z^T Hvt_{k-2} (K x SMAX)
 };
 
 // Per-chunk partial sums of up to 64 components, one warp total each, written to part[chunk][off + m].
@@ -426,6 +437,213 @@ __global__ void k_finalize(KrylovArgs a, T* w, const T* U, const int* mask) {
   }
 }
 
+
+// ---------------------------------------------------------------------------------------------
+// MINRES kernels
+
+// beta_1 = ||r_0||, zeta_0 = beta_1, rotations (c, s)_{0} = (1, 0), (c, s)_{-1} = (0, 0); s-vector
+// histories cleared
+__global__ void k_mr_start(KrylovArgs a, const int* mask) {
+  const int k = blockIdx.x;
+  if (!mask[k]) return;
+  for (int m = threadIdx.x; m < a.SMAX; m += blockDim.x) {
+    const size_t i = (size_t)k * a.SMAX + m;
+    a.b1[i] = a.b2[i] = a.h1[i] = a.h2[i] = 0.0;
+  }
+  if (threadIdx.x == 0) {
+    SolveState S = a.st[k];
+    S.beta_l = sqrt(fmax(S.rho, 0.0));
+    S.zeta = S.beta_l;
+    S.cm1 = 1.0;
+    S.sm1 = 0.0;
+    S.cm2 = 0.0;
+    S.sm2 = 0.0;
+    S.inv_bn = S.beta_l > 0.0 ? 1.0 / S.beta_l : 0.0;
+    a.st[k] = S;
+  }
+}
+
+// v_1 = r_0 / beta_1 (in place: the init left p = r_0), v_0 = vt_0 = vt_{-1} = 0
+template <typename T>
+__global__ void k_mr_vinit(KrylovArgs a, T* v, T* vprev, T* y1, T* y2, const int* mask) {
+  const ChunkDev ch = a.chunks[blockIdx.x];
+  if (!mask[ch.pair]) return;
+  const PairDev pr = a.pairs[ch.pair];
+  const T sc = (T)a.st[ch.pair].inv_bn;
+  for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
+    const long long gi = pr.off + ch.start + t;
+    v[gi] = v[gi] * sc;
+    vprev[gi] = T(0);
+    y1[gi] = T(0);
+    y2[gi] = T(0);
+  }
+}
+
+// alpha_k = v_k^T H v_k, C^T H v_k into c, Z^T H v_k into e (from the Hessian-action partials)
+__global__ void k_mr_scalar1(KrylovArgs a, int use_tiles, int nsc) {
+  const int k = blockIdx.x;
+  if (!a.st[k].active) return;
+  const PairDev pr = a.pairs[k];
+  const int s = a.s_k[k];
+  const int nz = (nsc && a.hasz[k]) ? s : 0;
+  const int ncomp = 1 + 2 * a.SMAX;
+  const double* part = use_tiles ? a.tpart : a.cpart;
+  const int beg = use_tiles ? pr.tbeg : pr.cbeg, end = use_tiles ? pr.tend : pr.cend;
+  for (int m = threadIdx.x; m < 1 + s + nz; m += blockDim.x) {
+    const int slot = m <= s ? m : 1 + a.SMAX + (m - 1 - s);
+    double t = 0.0;
+    for (int u = beg; u < end; ++u) t += part[(size_t)u * ncomp + slot];
+    if (m == 0) a.st[k].alpha = t;
+    else if (m <= s) a.c[k * a.SMAX + m - 1] = t;
+    else a.e[k * a.SMAX + m - 1 - s] = t;
+  }
+}
+
+// Lanczos: vn = H v_k - C (C^T H v_k) - alpha_k v_k - beta_k v_{k-1} (into r); partial ||vn||^2
+template <typename T>
+__global__ void k_mr_lanczos(KrylovArgs a, T* vn, const T* v, const T* vprev, const T* q, const T* C) {
+  __shared__ double red[40];
+  __shared__ T cs[64];
+  const ChunkDev ch = a.chunks[blockIdx.x];
+  const SolveState S = a.st[ch.pair];
+  if (!S.active) return;
+  const PairDev pr = a.pairs[ch.pair];
+  const int s = a.s_k[ch.pair];
+  if ((int)threadIdx.x < s) cs[threadIdx.x] = (T)a.c[ch.pair * a.SMAX + threadIdx.x];
+  __syncthreads();
+  const T* Cb = C + pr.off * a.SMAX;
+  const T al = (T)S.alpha, be = (T)S.beta_l;
+  Accum<T> acc;
+  for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
+    const long long li = ch.start + t, gi = pr.off + li;
+    T ccv = 0;
+    for (int j = 0; j < s; ++j) ccv = fma(cs[j], Cb[(long long)j * pr.n + li], ccv);
+    const T x = q[gi] - ccv - al * v[gi] - be * vprev[gi];
+    vn[gi] = x;
+    acc.add(x * x);
+  }
+  const double tot = block_total<kChunkThreads>(acc, red);
+  if (threadIdx.x == 0) a.cpart[blockIdx.x] = tot;
+}
+
+// beta_{k+1}, the Givens rotation of step k, zeta_k, the s-vector recurrences and the stopping test
+__global__ void k_mr_scalar2(KrylovArgs a, int stop_nsc, int* flag) {
+  __shared__ double sh[8];
+  __shared__ double bt[64];
+  const int k = blockIdx.x;
+  if (!a.st[k].active) return;
+  const PairDev pr = a.pairs[k];
+  const int s = a.s_k[k];
+  const int nz = (stop_nsc && a.hasz[k]) ? s : 0;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int u = pr.cbeg; u < pr.cend; ++u) t += a.cpart[u];
+    SolveState S = a.st[k];
+    const double bn = sqrt(fmax(t, 0.0));
+    const double gam = S.sm2 * S.beta_l;
+    const double del = S.cm1 * S.cm2 * S.beta_l + S.sm1 * S.alpha;
+    const double eps = -S.sm1 * S.cm2 * S.beta_l + S.cm1 * S.alpha;
+    const double et = hypot(eps, bn);
+    const double ck = et > 0.0 ? eps / et : 1.0, sk = et > 0.0 ? bn / et : 0.0;
+    const double zprev = S.zeta;
+    S.zeta = -sk * zprev;
+    S.gam = gam;
+    S.del = del;
+    S.inv_et = et > 0.0 ? 1.0 / et : 0.0;
+    S.coef = ck * zprev;
+    S.inv_bn = bn > 0.0 ? 1.0 / bn : 0.0;
+    S.cm2 = S.cm1;
+    S.sm2 = S.sm1;
+    S.cm1 = ck;
+    S.sm1 = sk;
+    S.beta_l = bn;
+    S.iters += 1;
+    if (!(et > 0.0) || !isfinite(et)) {
+      S.active = 0;
+      S.status = BL_EBREAKDOWN;
+      S.coef = 0.0;
+    }
+    a.st[k] = S;
+    sh[0] = S.gam;
+    sh[1] = S.del;
+    sh[2] = S.inv_et;
+    sh[3] = S.coef;
+  }
+  __syncthreads();
+  const double gam = sh[0], del = sh[1], iet = sh[2], coef = sh[3];
+  // beta~_k = (C^T H v_k - gamma beta~_{k-2} - delta beta~_{k-1}) / eps~;  z -= c_k zeta_{k-1} beta~_k
+  for (int m = threadIdx.x; m < s; m += blockDim.x) {
+    const size_t i = (size_t)k * a.SMAX + m;
+    const double b = (a.c[i] - gam * a.b2[i] - del * a.b1[i]) * iet;
+    a.b2[i] = a.b1[i];
+    a.b1[i] = b;
+    a.zc[i] -= coef * b;
+    bt[m] = b;
+  }
+  __syncthreads();
+  // Z^T Hvt_k = (Z^T H v_k - gamma Z^T Hvt_{k-2} - delta Z^T Hvt_{k-1}) / eps~;
+  // Z^T res -= c_k zeta_{k-1} (Z^T Hvt_k - (Z^T C) beta~_k)
+  for (int m = threadIdx.x; m < nz; m += blockDim.x) {
+    const size_t i = (size_t)k * a.SMAX + m;
+    const double h = (a.e[i] - gam * a.h2[i] - del * a.h1[i]) * iet;
+    a.h2[i] = a.h1[i];
+    a.h1[i] = h;
+    double zc = 0.0;
+    for (int j = 0; j < s; ++j) zc += a.ztc[((size_t)k * a.SMAX + m) * a.SMAX + j] * bt[j];
+    a.ztr[i] -= coef * (h - zc);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    SolveState S = a.st[k];
+    if (S.active) {
+      if (nz > 0) {
+        double z2 = 0.0;
+        for (int m = 0; m < nz; ++m) z2 += a.ztr[k * a.SMAX + m] * a.ztr[k * a.SMAX + m];
+        S.est = sqrt(z2);
+      } else {
+        S.est = fabs(S.zeta);
+      }
+      S.rho = S.zeta * S.zeta;
+      if (!isfinite(S.est)) {
+        S.active = 0;
+        S.status = BL_EBREAKDOWN;
+      } else if (S.est < S.tol || S.beta_l == 0.0) {
+        S.active = 0;
+      } else if (S.iters >= S.maxit) {
+        S.active = 0;
+        S.status = BL_ENOCONV;
+      }
+      a.st[k] = S;
+      if (S.active) atomicAdd(flag, 1);
+    }
+  }
+}
+
+// vt_k = (v_k - gamma vt_{k-2} - delta vt_{k-1}) / eps~; w += c_k zeta_{k-1} vt_k; V[:, k] = v_k;
+// v_{k-1} <- v_k; v_{k+1} = vn / beta_{k+1}.  Runs for the pairs active at the start of the step.
+template <typename T>
+__global__ void k_mr_update(KrylovArgs a, const int* itmask, T* w, T* v, T* vprev, const T* vn, T* y1, T* y2,
+                            T* V, int store) {
+  const ChunkDev ch = a.chunks[blockIdx.x];
+  if (!itmask[ch.pair]) return;
+  const SolveState S = a.st[ch.pair];
+  const PairDev pr = a.pairs[ch.pair];
+  T* Vc = store ? V + pr.off * a.KMAX + (long long)((S.iters - 1) % a.KMAX) * pr.n : nullptr;
+  const T gam = (T)S.gam, del = (T)S.del, iet = (T)S.inv_et, coef = (T)S.coef, ibn = (T)S.inv_bn;
+  for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
+    const long long li = ch.start + t, gi = pr.off + li;
+    const T vk = v[gi];
+    const T yo1 = y1[gi];
+    const T y = (vk - gam * y2[gi] - del * yo1) * iet;
+    w[gi] = fma(coef, y, w[gi]);
+    y2[gi] = yo1;
+    y1[gi] = y;
+    if (store) Vc[li] = vk;
+    vprev[gi] = vk;
+    v[gi] = vn[gi] * ibn;
+  }
+}
+
 // WHILE-node condition: another body run while some pair is active and the hard cap is not reached.
 __global__ void k_loop_cond(cudaGraphConditionalHandle h, const int* flag, int* loop) {
   const int ran = ++loop[0];
@@ -503,12 +721,22 @@ template <typename T>
 static bl_status solve_impl(bl_problem* P, const int* mask_host, const bl_krylov_opts* o, const void* g,
                             const double* nsc_scale, std::vector<bl_solve_info>& info) {
   const int K = P->K;
+  const bool minres = o->method == BL_SOLVE_MINRES || o->method == BL_SOLVE_RMINRES;
+  const bool recyc = o->method == BL_SOLVE_RCG || o->method == BL_SOLVE_RMINRES;
   // effective recycle dims and NSC flags for this solve
   std::vector<int> s_eff(K, 0), hz_eff(K, 0);
   for (int k = 0; k < K; ++k) {
     if (!mask_host[k]) continue;
-    s_eff[k] = (o->method == BL_SOLVE_RCG) ? P->s_k[k] : 0;
-    hz_eff[k] = (o->method == BL_SOLVE_RCG && o->stop == BL_STOP_NSC && P->hz_k[k]) ? 1 : 0;
+    s_eff[k] = recyc ? P->s_k[k] : 0;
+    hz_eff[k] = (recyc && o->stop == BL_STOP_NSC && P->hz_k[k]) ? 1 : 0;
+  }
+  if (minres && !P->mv_prev) {
+    const size_t nb = (size_t)P->n_tot * P->esz;
+    bl_status sa = dalloc(&P->mv_prev, nb);
+    if (sa == BL_OK) sa = dalloc(&P->my1, nb);
+    if (sa == BL_OK) sa = dalloc(&P->my2, nb);
+    if (sa == BL_OK) sa = dalloc((void**)&P->mrs, (size_t)4 * K * std::max(P->SMAX, 1) * sizeof(double));
+    if (sa != BL_OK) return sa;
   }
   int* d_seff = P->d_cols;          // reuse: per-pair ints
   int* d_hz = P->d_cols + K;
@@ -543,6 +771,13 @@ static bl_status solve_impl(bl_problem* P, const int* mask_host, const bl_krylov
   a.tpart = P->tpart;
   a.n_tiles = P->n_tiles;
   a.n_chunks = P->n_chunks;
+  if (minres) {
+    const size_t ks = (size_t)K * std::max(P->SMAX, 1);
+    a.b1 = P->mrs;
+    a.b2 = P->mrs + ks;
+    a.h1 = P->mrs + 2 * ks;
+    a.h2 = P->mrs + 3 * ks;
+  }
   const int* mask = P->d_active;
   T* w = (T*)P->w;
   T* r = (T*)P->r;
@@ -570,6 +805,12 @@ static bl_status solve_impl(bl_problem* P, const int* mask_host, const bl_krylov
   k_scalar_init2<<<K, 128, 0, P->stream>>>(a, mask, o->stop == BL_STOP_NSC ? 1 : 0, o->tol, o->relative,
                                            nsc_scale ? d_scale : nullptr, o->maxit, P->d_flag);
   BL_LAUNCH_CHECK(P);
+  if (minres) {
+    k_mr_start<<<K, 64, 0, P->stream>>>(a, mask);
+    BL_LAUNCH_CHECK(P);
+    k_mr_vinit<T><<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a, p, (T*)P->mv_prev, (T*)P->my1, (T*)P->my2, mask);
+    BL_LAUNCH_CHECK(P);
+  }
   }
   BL_CUDA_TRY(cudaMemcpyAsync(P->h_flag, P->d_flag, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
   BL_CUDA_TRY(cudaStreamSynchronize(P->stream));
@@ -605,11 +846,42 @@ static bl_status solve_impl(bl_problem* P, const int* mask_host, const bl_krylov
     BL_LAUNCH_CHECK(P);
     return BL_OK;
   };
+  // MINRES step: q = H v_k (with v^T q, C^T q and, for the NSC rule, Z^T q), Lanczos vector,
+  // rotation and stopping test, direction and solution update
+  auto mr_iteration = [&]() -> bl_status {
+    {
+      ProfScope ps(P, BL_KC_KRYLOV);
+      k_copy_active<<<1, 128, 0, P->stream>>>(P->st, d_itmask, K);
+      BL_LAUNCH_CHECK(P);
+    }
+    const int* zflags = nsc ? d_hz : d_nohz;
+    bl_status s2 = launch_hvp(P, p, q, 0, 0, d_itmask, fused ? d_seff : nullptr, fused ? zflags : nullptr);
+    if (s2 != BL_OK) return s2;
+    ProfScope ps(P, BL_KC_KRYLOV);
+    if (!fused) {
+      KrylovArgs a0 = a;
+      a0.hasz = zflags;
+      k_dots<T><<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a0, p, q, C, Z);
+      BL_LAUNCH_CHECK(P);
+    }
+    k_mr_scalar1<<<K, 128, 0, P->stream>>>(a, fused ? 1 : 0, nsc);
+    BL_LAUNCH_CHECK(P);
+    k_mr_lanczos<T><<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a, r, p, (const T*)P->mv_prev, q, C);
+    BL_LAUNCH_CHECK(P);
+    BL_CUDA_TRY(cudaMemsetAsync(P->d_flag, 0, sizeof(int), P->stream));
+    k_mr_scalar2<<<K, 64, 0, P->stream>>>(a, nsc, P->d_flag);
+    BL_LAUNCH_CHECK(P);
+    k_mr_update<T><<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a, d_itmask, w, p, (T*)P->mv_prev, r, (T*)P->my1,
+                                                                 (T*)P->my2, (T*)P->V, store);
+    BL_LAUNCH_CHECK(P);
+    return BL_OK;
+  };
+  auto step = [&]() -> bl_status { return minres ? mr_iteration() : iteration(); };
   bool use_graph = *P->h_flag > 0 && o->graph && !P->prof && !P->graph_failed;
   if (use_graph) {
-    const KrylovGraphKey key{fused, store, nsc, P->tpart, P->cpart, P->V};
+    const KrylovGraphKey key{fused, store, nsc, minres ? 1 : 0, P->tpart, P->cpart, P->V};
     if (!P->kgraph || !(P->kgraph->key == key)) {
-      if (build_krylov_graph(P, key, iteration) != BL_OK) {
+      if (build_krylov_graph(P, key, step) != BL_OK) {
         // the stream path below runs the same kernels; remember not to retry the capture
         P->graph_error = error_copy();
         P->graph_failed = true;
@@ -632,7 +904,7 @@ static bl_status solve_impl(bl_problem* P, const int* mask_host, const bl_krylov
     P->launches += (int64_t)ran * P->kgraph->body_kernels + 1;
   } else {
     for (int it = 0; it < o->maxit && *P->h_flag > 0; ++it) {
-      st = iteration();
+      st = step();
       if (st != BL_OK) return st;
       BL_CUDA_TRY(cudaMemcpyAsync(P->h_flag, P->d_flag, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
       BL_CUDA_TRY(cudaStreamSynchronize(P->stream));

@@ -179,7 +179,7 @@ void bl_problem_destroy(bl_problem* P) {
                   P->d_active, P->d_cols, P->d_flag, P->dG, P->dT, P->dJ, P->dY, P->dY2, P->dY3, P->d_tk,
                   P->lx, P->lg, P->ld, P->lxt, P->lgt, P->lq, P->S, P->Yh, P->lsy, P->lyy, P->lcs, P->lcy,
                   P->lst, P->tpart, P->cpart, P->vals,
-                  P->d_pix, P->d_zero, P->d_loop};
+                  P->d_pix, P->d_zero, P->d_loop, P->mv_prev, P->my1, P->my2, P->mrs};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (P->h_flag) cudaFreeHost(P->h_flag);
@@ -498,7 +498,7 @@ bl_status bl_hessian_solve(bl_problem* P, const int32_t* pairs, int32_t npairs, 
   if (!P->point_set) return fail(BL_ESTATE, "no point set: call bl_set_point or bl_lower_solve first");
   bl_status st = check_pairs(P, pairs, npairs);
   if (st != BL_OK) return st;
-  if (o->method != BL_SOLVE_CG && o->method != BL_SOLVE_RCG) return fail(BL_EINVAL, "unknown solve method");
+  if (o->method < BL_SOLVE_CG || o->method > BL_SOLVE_RMINRES) return fail(BL_EINVAL, "unknown solve method");
   if (o->stop != BL_STOP_RESID && o->stop != BL_STOP_NSC) return fail(BL_EINVAL, "unknown stop rule");
   if (o->maxit < 0 || !(o->tol >= 0.0)) return fail(BL_EINVAL, "invalid Krylov options");
   if ((st = set_active_pairs(P, pairs, npairs)) != BL_OK) return st;
