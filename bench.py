@@ -29,25 +29,27 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-S_RECYCLE = 16
+S_RECYCLE = 16         # recycle dimension of the 64-pair batch (30 for the inpainting batch)
 MAX_BASIS = 32
 RTOL = 1e-4            # residual stopping tolerance (relative to ||g||)
+INPAINT_RTOL = 1e-5
 LOWER_GTOL = 1e-5      # lower-level gradient tolerance (relative to ||grad Phi(0)||)
 ADAM_LR = 1e-2
 FP32_FMA_LANES = 152 * 128   # GB300: 152 SMs x 128 FP32 lanes
 
 
-def hvp_flops_per_pixel(n_filters, f, rb):
+def hvp_flops_per_pixel(n_filters, f, rb, masked=False):
     """Algorithmic FP32 flops of one Hessian action per pixel (fields variant):
     per filter K v (2 T), times d_j (1), K^T (2 T); blur A A v separable (4 passes x (2 r_b + 1)
-    FMA = 8 (2 r_b + 1) flop); l2 term and sum (2)."""
+    FMA = 8 (2 r_b + 1) flop), or for inpainting the mask product (2); l2 term and sum (2)."""
     T = f * f
-    return n_filters * (4 * T + 1) + 8 * (2 * rb + 1) + 2
+    return n_filters * (4 * T + 1) + (2 if masked else 8 * (2 * rb + 1)) + 2
 
 
-def hvp_bytes_per_pixel(n_filters, esz=4):
-    """Algorithmic HBM bytes of one Hessian action per pixel: v in, H v out, N fields d_j in."""
-    return (2 + n_filters) * esz
+def hvp_bytes_per_pixel(n_filters, esz=4, masked=False):
+    """Algorithmic HBM bytes of one Hessian action per pixel: v in, H v out, N fields d_j in (and
+    the 1-byte mask for inpainting)."""
+    return (2 + n_filters) * esz + (1 if masked else 0)
 
 
 class Clocks:
@@ -101,6 +103,23 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------------------------
+# Workloads
+
+def make_workload(name, replica=0):
+    """(workload, recycle dimension, description) for --workload.  The residual tolerance that
+    keeps every hypergradient within 1e-4 is RTOL for the batch and INPAINT_RTOL for the
+    inpainting pairs (70 % unmeasured pixels make their Hessians ill-conditioned: rtol 1e-4 left
+    errors of 2-3e-4)."""
+    from paper_2412_08264_gb300 import synth
+    if name == "inpaint":
+        wl = synth.inpaint_batch(seed=replica)
+        return wl, 30, (f"inpaint1024x28_n3f5: {len(wl.pairs)} pairs of 28x28, 30 % of pixels measured, "
+                        f"noise 0.1, 3 5x5 filters, phi = s^2, p={wl.n_params}")
+    wl = synth.batch_64(replica=replica)
+    return wl, S_RECYCLE, None
+
+
+# ---------------------------------------------------------------------------------------------
 # GPU arm
 
 def gpu_arm(args, rank, world, dist):
@@ -111,7 +130,8 @@ def gpu_arm(args, rank, world, dist):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    wl = synth.batch_64(replica=rank)
+    wl, s_rec, wdesc = make_workload(args.workload, replica=rank)
+    rtol = INPAINT_RTOL if args.workload == "inpaint" else RTOL
     if args.pairs and args.pairs < len(wl.pairs):
         wl.pairs, wl.x_star, wl.noise = wl.pairs[:args.pairs], wl.x_star[:args.pairs], wl.noise[:args.pairs]
     K = len(wl.pairs)
@@ -119,14 +139,17 @@ def gpu_arm(args, rank, world, dist):
     nz_h = torch.tensor(np.concatenate([x.ravel() for x in wl.noise]), dtype=torch.float32).pin_memory()
     xs = xs_h.to(dev)
     P0 = api.from_workload(wl, xs, xs)
-    y = P0.forward(xs) + nz_h.to(dev)
+    if any(m is not None for m in wl.masks):
+        y = P0.forward(xs + nz_h.to(dev))     # inpainting: noisy values at the measured pixels only
+    else:
+        y = P0.forward(xs) + nz_h.to(dev)
     del P0
     y_h = y.cpu().pin_memory()
     n_pix = xs.numel()
     strategy = parse(args.strategy)
 
     def run(strat, steps, warmup, e2e=False, validate=False, profile_range=False, prof_steps=0):
-        P = api.from_workload(wl, y, xs, max_recycle=S_RECYCLE, max_basis=args.max_basis)
+        P = api.from_workload(wl, y, xs, max_recycle=s_rec, max_basis=args.max_basis)
         y_d = torch.empty_like(y)
         xs_d = torch.empty_like(xs)
         theta = wl.theta0.copy()
@@ -148,10 +171,11 @@ def gpu_arm(args, rank, world, dist):
                 P.set_data(y_d, xs_d)
             P.lower_solve(theta_d, xhat, gtol=LOWER_GTOL, relative=True, max_iters=2000, allow_noconv=True)
             if strat.recycles and state["t"] > 0:
-                P.ritz_update(strat, S_RECYCLE)
-            info = P.hessian_solve(w, recycle=strat.recycles, nsc=strat.nsc, tol=RTOL, relative=True, maxit=3000,
+                P.ritz_update(strat, s_rec)
+            info = P.hessian_solve(w, recycle=strat.recycles, nsc=strat.nsc, tol=rtol, relative=True, maxit=3000,
                                    store_basis=strat.recycles, warm_start=True,
-                                   nsc_scale=None if hg_prev is None else [hg_prev] * K, allow_noconv=True)
+                                   nsc_scale=None if hg_prev is None else [hg_prev] * K, allow_noconv=True,
+                                   method=args.method)
             mean, per = P.hypergrad(w, per_pair=True)
             if world > 1:
                 mean = allreduce_mean(mean, K)
@@ -229,14 +253,14 @@ def gpu_arm(args, rank, world, dist):
     cg = (run(parse("none"), args.steps, args.warmup, validate=True, prof_steps=args.prof_steps)
           if (args.compare_cg and strategy.recycles) else None)
     e2e = run(strategy, args.steps, args.warmup, e2e=True) if args.e2e else None
-    return dict(rec=rec, cg=cg, e2e=e2e, K=K, n_pix=n_pix, wl=wl, strategy=strategy)
+    return dict(rec=rec, cg=cg, e2e=e2e, K=K, n_pix=n_pix, wl=wl, strategy=strategy, s_rec=s_rec, wdesc=wdesc)
 
 
 # ---------------------------------------------------------------------------------------------
 # CPU checker arm (bounded sample)
 
-def oracle_sample(steps, warmup, max_seconds=None, strategy="RGen-L(R)"):
-    """Run the FP64 checker on one 128x128 pair of the batch for warmup + steps outer steps.
+def oracle_sample(steps, warmup, max_seconds=None, strategy="RGen-L(R)", workload="batch64"):
+    """Run the FP64 checker on the smallest pair of the batch for warmup + steps outer steps.
     Returns (seconds per timed step, sample description)."""
     from paper_2412_08264_gb300 import synth
     from paper_2412_08264_gb300.strategy import parse
@@ -244,9 +268,9 @@ def oracle_sample(steps, warmup, max_seconds=None, strategy="RGen-L(R)"):
     from oracle.krylov import rcg
     from oracle.recycle import refresh
 
-    wl = synth.batch_64()
+    wl, s_rec, _ = make_workload(workload)
     k0 = min(range(len(wl.pairs)), key=lambda k: wl.pairs[k].height * wl.pairs[k].width)
-    wl.pairs, wl.x_star, wl.noise = [wl.pairs[k0]], [wl.x_star[k0]], [wl.noise[k0]]
+    wl.pairs, wl.x_star, wl.noise, wl.masks = [wl.pairs[k0]], [wl.x_star[k0]], [wl.noise[k0]], [wl.masks[k0]]
     prob = BilevelProblem(wl)
     st = parse(strategy)
     ll = prob.lowers[0]
@@ -264,7 +288,7 @@ def oracle_sample(steps, warmup, max_seconds=None, strategy="RGen-L(R)"):
         AH = prob.apply_H(0, x, theta)
         if st.recycles and V is not None:
             Up = U if U is not None else np.zeros((ll.n, 0))
-            U, C, Z, _ = refresh(Up, V, AH, lambda v: prob.Jw(0, x, theta, v), S_RECYCLE, st.kind, st.size, st.side)
+            U, C, Z, _ = refresh(Up, V, AH, lambda v: prob.Jw(0, x, theta, v), s_rec, st.kind, st.size, st.side)
         g = prob.rhs(0, x)
         out = rcg(AH, g, w, U, C, tol=RTOL * np.linalg.norm(g), maxit=3000, kmax_store=MAX_BASIS)
         w, V = out["w"], out["V"]
@@ -275,7 +299,8 @@ def oracle_sample(steps, warmup, max_seconds=None, strategy="RGen-L(R)"):
             times.append(dt)
         if max_seconds is not None and sum(times) > max_seconds and len(times) >= 1:
             break
-    desc = (f"pair {k0} of the 64-pair batch ({ll.h}x{ll.w}, 16 5x5 filters), {strategy}, "
+    desc = (f"pair {k0} of the {workload} batch ({ll.h}x{ll.w}, {wl.n_filters} {wl.filter_size}x{wl.filter_size} "
+            f"filters), {strategy}, "
             f"{warmup} warm-up + {len(times)} timed outer steps, FP64 NumPy")
     return float(np.mean(times)), len(times), desc
 
@@ -289,6 +314,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--strategy", default="RGen-L(R)")
+    ap.add_argument("--workload", default="batch64", choices=["batch64", "inpaint"],
+                    help="batch64: the 64-pair deconvolution batch (the metric's workload); inpaint: 1024 "
+                         "inpainting pairs shaped like the paper's Section 5.1 experiment")
+    ap.add_argument("--method", default="cg", choices=["cg", "minres"],
+                    help="Krylov method of the Hessian solves: (recycled) CG or (recycled) MINRES")
     ap.add_argument("--max-basis", type=int, default=MAX_BASIS,
                     help="Krylov basis vectors kept per pair for the next refresh")
     ap.add_argument("--no-compare-cg", dest="compare_cg", action="store_false")
@@ -310,13 +340,15 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        sec, n, desc = oracle_sample(args.steps, args.warmup, strategy=args.strategy)
+        sec, n, desc = oracle_sample(args.steps, args.warmup, strategy=args.strategy, workload=args.workload)
         v = 1.0 / sec
         print(json.dumps({"impl": "reference", "metric": metric, "value": v, "unit": "hypergradients/s",
                           "n_gpus": args.gpus, "steps": n, "warmup": args.warmup, "ms_per_step": sec * 1e3,
                           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                           "data": "synthetic",
-                          "config": {"workload": "batch64_foe_n16f5 (sample)", "strategy": args.strategy},
+                          "config": {"workload": ("batch64_foe_n16f5" if args.workload == "batch64"
+                                                  else "inpaint1024x28_n3f5") + " (sample)",
+                                     "strategy": args.strategy},
                           "cpu_baseline": {"value": v, "unit": "hypergradients/s", "cores": os.cpu_count(),
                                            "kind": "oracle", "sample": desc},
                           "e2e": {"value": v, "unit": "hypergradients/s", "h2d_bytes_per_step": 0,
@@ -346,8 +378,9 @@ def main():
     profd = rec["prof"] or {k: zero for k in ["hvp", "hvp_multi", "grad", "jw", "krylov", "lbfgs", "gram", "gemm",
                                                "dense", "other"]}
     hv = profd["hvp"]
-    fpp = hvp_flops_per_pixel(wl.n_filters, wl.filter_size, wl.pairs[0].blur_radius)
-    bpp = hvp_bytes_per_pixel(wl.n_filters)
+    masked = any(m is not None for m in wl.masks)
+    fpp = hvp_flops_per_pixel(wl.n_filters, wl.filter_size, wl.pairs[0].blur_radius, masked)
+    bpp = hvp_bytes_per_pixel(wl.n_filters, masked=masked)
     avg_ms = hv["ms"] / max(1, hv["launches"])
     flops_per_launch = fpp * hv["pixels"] / max(1, hv["launches"])
     achieved_tflops = flops_per_launch / (avg_ms / 1e3) / 1e12
@@ -358,10 +391,10 @@ def main():
         "metric": metric, "value": value, "unit": "hypergradients/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"batch64_foe_n16f5: {K} pairs, sides 128-512, {n_pix} px, 16 5x5 filters, "
-                               f"9x9 blur, p={wl.n_params}",
-                   "strategy": out["strategy"].acronym(), "recycle_dim": S_RECYCLE, "max_basis": args.max_basis,
-                   "stop": f"residual rtol {RTOL}", "lower_gtol_rel": LOWER_GTOL, "outer": "Adam lr 1e-2",
+        "config": {"workload": out["wdesc"] or (f"batch64_foe_n16f5: {K} pairs, sides 128-512, {n_pix} px, "
+                                                f"16 5x5 filters, 9x9 blur, p={wl.n_params}"),
+                   "strategy": out["strategy"].acronym(), "krylov": args.method, "recycle_dim": out["s_rec"], "max_basis": args.max_basis,
+                   "stop": f"residual rtol {INPAINT_RTOL if args.workload == 'inpaint' else RTOL}", "lower_gtol_rel": LOWER_GTOL, "outer": "Adam lr 1e-2",
                    "l2": "inputs larger than L2 (batch working set > 1 GB), no flush"},
         "hg_rel_err_max": rec.get("hg_err_max"), "hg_rel_err_mean_grad": rec.get("hg_err_mean_grad"),
         "krylov_iters_per_step": [int(np.max(it)) for it in rec["iters"]],
@@ -394,7 +427,7 @@ def main():
         line["e2e"] = {"value": K * world * args.steps / (ms_e / 1e3), "unit": "hypergradients/s",
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": wl.n_params * 8}
     if rank == 0 and world == 1 and args.cpu_baseline:
-        sec, n, desc = oracle_sample(2, 1, max_seconds=30.0, strategy=args.strategy)
+        sec, n, desc = oracle_sample(2, 1, max_seconds=30.0, strategy=args.strategy, workload=args.workload)
         line["cpu_baseline"] = {"value": 1.0 / sec, "unit": "hypergradients/s", "cores": os.cpu_count(),
                                 "kind": "oracle", "sample": desc}
     if rank == 0:

@@ -57,12 +57,17 @@ typedef enum { BL_REG_TV = 0, BL_REG_FOE = 1 } bl_reg_kind;
 typedef enum { BL_PHI_CHARBONNIER = 0, BL_PHI_SQ = 1, BL_PHI_LOG1P = 2 } bl_phi_kind;
 typedef enum { BL_FP32 = 0, BL_FP64 = 1 } bl_precision;
 
-/* One training pair: image size and its Gaussian blur A (Section 5.2):
- * G[a, b] proportional to exp(-(a^2 + b^2) / (2 sigma^2)) on [-r_b, r_b]^2, summing to 1. */
+/* One training pair: image size and its forward operator A.
+ *   mask == NULL: the Gaussian blur of Section 5.2, G[a, b] proportional to
+ *                 exp(-(a^2 + b^2) / (2 sigma^2)) on [-r_b, r_b]^2, summing to 1.
+ *   mask != NULL: inpainting (Section 5.1): A keeps the measured pixels, A = diag(mask != 0) on
+ *                 the image grid (measurements y are zero elsewhere); host, height * width bytes,
+ *                 row-major, copied at create; blur_sigma and blur_radius are ignored. */
 typedef struct {
   int32_t height, width;
   double blur_sigma;
   int32_t blur_radius;
+  const uint8_t* mask;
 } bl_pair_desc;
 
 /* Lower-level functional (eq. (1.1) with the eps term of eq. (5.1)):
@@ -142,7 +147,7 @@ typedef struct bl_problem bl_problem;
 /* Create a problem for K pairs (Section 5, eq. (5.2)).
  * y_packed, xstar_packed: device, packed over pairs 0..K-1, precision's scalar type; copied.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream) that all later work runs on.
- * Returns BL_EINVAL for K < 1, sizes < 1, filter size even or > 7, blur radius > 4,
+ * Returns BL_EINVAL for K < 1, sizes < 1, filter size even or > 7, blur radius > 4 (blur pairs),
  * n_filters < 1 (FoE), unknown enum values or a null pointer. */
 bl_status bl_problem_create(const bl_pair_desc* pairs, int32_t K, const bl_reg_desc* reg,
                             const void* y_packed, const void* xstar_packed, void* cuda_stream,

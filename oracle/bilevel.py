@@ -26,12 +26,18 @@ class BilevelProblem:
         self.K = len(wl.pairs)
         self.lowers = []
         self.ys = []
-        for spec, xs, nz in zip(wl.pairs, wl.x_star, wl.noise):
-            G = ops.gaussian_kernel(spec.blur_sigma, spec.blur_radius)
-            y = ops.blur(xs, G) + nz
+        masks = (list(getattr(wl, "masks", None) or []) + [None] * self.K)[:self.K]
+        for spec, xs, nz, m in zip(wl.pairs, wl.x_star, wl.noise, masks):
+            if m is not None:
+                # inpainting (Section 5.1): only the measured pixels carry data
+                G = None
+                y = (m != 0) * (xs + nz)
+            else:
+                G = ops.gaussian_kernel(spec.blur_sigma, spec.blur_radius)
+                y = ops.blur(xs, G) + nz
             self.ys.append(y)
             self.lowers.append(LowerLevel(y, G, wl.reg, wl.n_filters, wl.filter_size,
-                                          wl.phi, wl.phi_eps, wl.l2_eps))
+                                          wl.phi, wl.phi_eps, wl.l2_eps, mask=m))
         self.x_star = wl.x_star
 
     @property

@@ -54,11 +54,13 @@ def phi_fns(kind: str, eps: float):
 class LowerLevel:
     def __init__(self, y: np.ndarray, G: np.ndarray, reg: str, n_filters: int = 0,
                  filter_size: int = 0, phi: str = "charbonnier", phi_eps: float = 0.01,
-                 l2_eps: float = 1e-6):
+                 l2_eps: float = 1e-6, mask: np.ndarray = None):
+        """G: blur kernel of A; or mask (0/1 per pixel): inpainting, A = diag(mask) (Section 5.1)."""
         self.y = np.asarray(y, dtype=np.float64)
         self.h, self.w = self.y.shape
         self.n = self.h * self.w
         self.G = G
+        self.mask = None if mask is None else (np.asarray(mask) != 0).astype(np.float64)
         self.reg = reg
         self.N = n_filters
         self.f = filter_size
@@ -80,9 +82,13 @@ class LowerLevel:
         return alphas, ks
 
     def A(self, x):
+        if self.mask is not None:
+            return self.mask * x
         return ops.blur(x, self.G)
 
     def At(self, u):
+        if self.mask is not None:
+            return self.mask * u
         return ops.blur_adjoint(u, self.G)
 
     # ---- value, gradient, Hessian action ------------------------------------------------
@@ -156,6 +162,8 @@ class LowerLevel:
 
     # ---- dense assembly (tiny images only) ---------------------------------------------
     def dense_A(self):
+        if self.mask is not None:
+            return np.diag(self.mask.reshape(-1))
         return ops.dense_correlation(self.G, self.h, self.w)
 
     def dense_hessian(self, x, theta) -> np.ndarray:

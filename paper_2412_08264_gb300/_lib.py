@@ -28,7 +28,7 @@ KERNEL_CLASSES = ["hvp", "hvp_multi", "grad", "jw", "krylov", "lbfgs", "gram", "
 
 class PairDesc(C.Structure):
     _fields_ = [("height", C.c_int32), ("width", C.c_int32), ("blur_sigma", C.c_double),
-                ("blur_radius", C.c_int32)]
+                ("blur_radius", C.c_int32), ("mask", C.c_void_p)]
 
 
 class RegDesc(C.Structure):

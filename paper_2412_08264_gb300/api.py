@@ -10,6 +10,7 @@ from __future__ import annotations
 import ctypes as C
 from typing import Optional, Sequence
 
+import numpy as np
 import torch
 
 from . import _lib as L
@@ -24,13 +25,28 @@ class Problem:
     def __init__(self, pairs: Sequence, reg: str, y: torch.Tensor, x_star: torch.Tensor, n_filters: int = 0,
                  filter_size: int = 0, phi: str = "charbonnier", phi_eps: float = 0.01, l2_eps: float = 1e-6,
                  precision: str = "fp32", max_recycle: int = 0, max_basis: int = 0):
-        """pairs: sequence of (height, width, blur_sigma, blur_radius)."""
+        """pairs: sequence of (height, width, blur_sigma, blur_radius) for blur pairs, or
+        (height, width, blur_sigma, blur_radius, mask) with mask an (height, width) array of
+        measured pixels (non-zero) for inpainting pairs (blur fields then ignored)."""
         self.lib = L.load()
         self.K = len(pairs)
         self.sizes = [(int(p[0]), int(p[1])) for p in pairs]
         self.dtype = torch.float32 if precision == "fp32" else torch.float64
         self.device = y.device
-        arr = (L.PairDesc * self.K)(*[L.PairDesc(int(h), int(w), float(s), int(r)) for h, w, s, r in pairs])
+        masks = []       # kept alive until bl_problem_create has copied them
+        descs = []
+        for p in pairs:
+            h, w, s, r = p[:4]
+            m = p[4] if len(p) > 4 else None
+            ptr = None
+            if m is not None:
+                m = np.ascontiguousarray((np.asarray(m) != 0).astype(np.uint8))
+                if m.shape != (int(h), int(w)):
+                    raise ValueError(f"mask shape {m.shape} does not match the image size {(h, w)}")
+                masks.append(m)
+                ptr = m.ctypes.data
+            descs.append(L.PairDesc(int(h), int(w), float(s), int(r), ptr))
+        arr = (L.PairDesc * self.K)(*descs)
         rd = L.RegDesc(L.BL_REG_TV if reg == "tv" else L.BL_REG_FOE, int(n_filters), int(filter_size),
                        L.BL_PHI[phi], float(phi_eps), float(l2_eps),
                        L.BL_FP32 if precision == "fp32" else L.BL_FP64, int(max_recycle), int(max_basis))
@@ -218,7 +234,8 @@ class Problem:
 
 def from_workload(wl, y: torch.Tensor, x_star: torch.Tensor, **kw) -> Problem:
     """Problem for a synth.Workload with given packed measurements and ground truths."""
-    pairs = [(p.height, p.width, p.blur_sigma, p.blur_radius) for p in wl.pairs]
+    masks = (list(getattr(wl, "masks", None) or []) + [None] * len(wl.pairs))[:len(wl.pairs)]
+    pairs = [(p.height, p.width, p.blur_sigma, p.blur_radius, m) for p, m in zip(wl.pairs, masks)]
     args = dict(reg=wl.reg, n_filters=wl.n_filters, filter_size=wl.filter_size, phi=wl.phi,
                 phi_eps=wl.phi_eps, l2_eps=wl.l2_eps, precision=wl.precision)
     args.update(kw)

@@ -51,6 +51,7 @@ __host__ __device__ constexpr int tile_out(int F) { return (kTileRegion - 2 * (F
 struct PairDev {
   int h, w;
   long long n, off;
+  const unsigned char* opm;   // inpainting: this pair's measured-pixel mask (A = diag(opm != 0)); null: blur
   int rb;
   int tbeg, tend;      // tiles [tbeg, tend) of this pair
   int cbeg, cend;      // chunks [cbeg, cend)
@@ -105,6 +106,7 @@ struct PairHost {
   long long n, off;
   int rb;
   double sigma;
+  bool masked;
   int tbeg, tend, cbeg, cend;
 };
 
@@ -142,6 +144,7 @@ struct bl_problem {
   // allocated on the first MINRES solve
   void *mv_prev = nullptr, *my1 = nullptr, *my2 = nullptr;
   double* mrs = nullptr;
+  unsigned char* d_opmask = nullptr;   // inpainting masks of all pairs (n_tot bytes), if any pair has one
   void *U = nullptr, *C = nullptr, *Z = nullptr, *V = nullptr;
   void *W = nullptr, *Wt = nullptr, *HWt = nullptr;
   bl::SolveState* st = nullptr;

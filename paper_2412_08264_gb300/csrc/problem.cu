@@ -179,7 +179,7 @@ void bl_problem_destroy(bl_problem* P) {
                   P->d_active, P->d_cols, P->d_flag, P->dG, P->dT, P->dJ, P->dY, P->dY2, P->dY3, P->d_tk,
                   P->lx, P->lg, P->ld, P->lxt, P->lgt, P->lq, P->S, P->Yh, P->lsy, P->lyy, P->lcs, P->lcy,
                   P->lst, P->tpart, P->cpart, P->vals,
-                  P->d_pix, P->d_zero, P->d_loop, P->mv_prev, P->my1, P->my2, P->mrs};
+                  P->d_pix, P->d_zero, P->d_loop, P->mv_prev, P->my1, P->my2, P->mrs, P->d_opmask};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (P->h_flag) cudaFreeHost(P->h_flag);
@@ -212,6 +212,7 @@ bl_status bl_problem_create(const bl_pair_desc* pairs, int32_t K, const bl_reg_d
     return fail(BL_EINVAL, "max_recycle + max_basis must be <= 96");
   for (int k = 0; k < K; ++k) {
     if (pairs[k].height < 1 || pairs[k].width < 1) return fail(BL_EINVAL, "image sizes must be >= 1");
+    if (pairs[k].mask) continue;   // inpainting pair: the blur fields are ignored
     if (pairs[k].blur_radius < 0 || pairs[k].blur_radius > BL_MAX_BLUR_RADIUS)
       return fail(BL_EINVAL, "blur_radius must be in 0..4");
     if (!(pairs[k].blur_sigma > 0.0)) return fail(BL_EINVAL, "blur_sigma must be > 0");
@@ -248,8 +249,9 @@ bl_status bl_problem_create(const bl_pair_desc* pairs, int32_t K, const bl_reg_d
     ph.w = pairs[k].width;
     ph.n = (long long)ph.h * ph.w;
     ph.off = off;
-    ph.rb = pairs[k].blur_radius;
-    ph.sigma = pairs[k].blur_sigma;
+    ph.masked = pairs[k].mask != nullptr;
+    ph.rb = ph.masked ? 0 : pairs[k].blur_radius;
+    ph.sigma = ph.masked ? 1.0 : pairs[k].blur_sigma;
     ph.tbeg = (int)tiles.size();
     for (int ty = 0; ty < ph.h; ty += TILE)
       for (int tx = 0; tx < ph.w; tx += TILE) tiles.push_back(TileDev{k, ty, tx});
@@ -304,8 +306,20 @@ bl_status bl_problem_create(const bl_pair_desc* pairs, int32_t K, const bl_reg_d
   BL_ALLOC(dalloc((void**)&P->d_tiles, tiles.size() * sizeof(TileDev)));
   BL_ALLOC(dalloc((void**)&P->d_chunks, chunks.size() * sizeof(ChunkDev)));
   for (void** b : {&P->y, &P->xstar, &P->xhat, &P->r, &P->pv, &P->q, &P->w, &P->g, &P->lx, &P->lg, &P->ld,
-                   &P->lxt, &P->lgt, &P->lq})
+                   &P->lxt, &P->lgt})
     BL_ALLOC(alloc_vec(P, b, n));
+  // inpainting masks: one byte per pixel of every pair (0 / 1), pointed to by the pair descriptors
+  std::vector<unsigned char> hmask;
+  for (int k = 0; k < K; ++k)
+    if (pairs[k].mask) {
+      if (hmask.empty()) {
+        BL_ALLOC(dalloc((void**)&P->d_opmask, n));
+        hmask.assign(n, 0);
+      }
+      const PairHost& ph = P->ph[k];
+      for (long long i = 0; i < ph.n; ++i) hmask[ph.off + i] = pairs[k].mask[i] ? 1 : 0;
+      pd[k].opm = P->d_opmask + ph.off;
+    }
   BL_ALLOC(alloc_vec(P, &P->tmp, 3 * n));
   if (P->N > 0) {
     BL_ALLOC(alloc_vec(P, &P->fu, (size_t)P->N * n));
@@ -354,6 +368,7 @@ bl_status bl_problem_create(const bl_pair_desc* pairs, int32_t K, const bl_reg_d
   };
   cudaError_t e = cudaSuccess;
   e = e == cudaSuccess ? cpy(P->d_pairs, pd.data(), K * sizeof(PairDev), cudaMemcpyHostToDevice) : e;
+  if (!hmask.empty()) e = e == cudaSuccess ? cpy(P->d_opmask, hmask.data(), n, cudaMemcpyHostToDevice) : e;
   e = e == cudaSuccess ? cpy(P->d_tiles, tiles.data(), tiles.size() * sizeof(TileDev), cudaMemcpyHostToDevice) : e;
   e = e == cudaSuccess ? cpy(P->d_chunks, chunks.data(), chunks.size() * sizeof(ChunkDev), cudaMemcpyHostToDevice) : e;
   e = e == cudaSuccess ? cpy(P->y, y_packed, n * P->esz, cudaMemcpyDeviceToDevice) : e;

@@ -150,6 +150,29 @@ __global__ void __launch_bounds__(kStencilThreads, sizeof(T) == 4 ? 2 : 1) k_foe
   for (int idx = tid; idx < a.N * F * F; idx += kStencilThreads) tps[idx] = a.taps[idx];
   __syncthreads();
 
+  const bool owner = tid < NB * NB;
+  const int oby = owner ? tid / NB : 0, obx = owner ? tid - (tid / NB) * NB : 0;
+  T outacc[4][4];
+  Accum<T> dterm;                                       // GRAD: ||A x - y||^2 over the tile
+  if (pr.opm) {
+    // ---- inpainting data term: A^T A = diag(m): 2 m v (HVP) or 2 m (x - y) (GRAD) ----
+#pragma unroll
+    for (int yy = 0; yy < 4; ++yy)
+#pragma unroll
+      for (int xx = 0; xx < 4; ++xx) {
+        const int iy = oy + 4 * oby + yy, ix = ox + 4 * obx + xx;
+        const T vv = vs[(4 * oby + yy + kHalo) * VD + 4 * obx + xx + kHalo];
+        T s = 0;
+        if (owner && 4 * oby + yy < TILE && 4 * obx + xx < TILE && iy < h && ix < w) {
+          const long long pl = (long long)iy * w + ix;
+          if (pr.opm[pl]) {
+            s = MODE == kModeGrad ? vv - a.y[pr.off + pl] : vv;
+            if (MODE == kModeGrad) dterm.add(s * s);
+          }
+        }
+        outacc[yy][xx] = T(2) * s + a.l2 * vv;
+      }
+  } else {
   // ---- blur part: A (A v) (HVP) or A (A x - y) (GRAD), separable passes in smem ----
   const int E2 = TILE + 2 * rb;                       // region of A v: tile grown by r_b
   T g[2 * BL_MAX_BLUR_RADIUS + 1];
@@ -167,7 +190,6 @@ __global__ void __launch_bounds__(kStencilThreads, sizeof(T) == 4 ? 2 : 1) k_foe
     h1[y * VD + x] = s;
   }
   __syncthreads();
-  Accum<T> dterm;                                       // GRAD: ||A x - y||^2 over the tile
   // av[i][x] = sum_a g[a] h1[i + a + sh][x], masked to the image (and minus y in GRAD mode)
   for (int idx = tid; idx < E2 * E2; idx += kStencilThreads) {
     const int i = idx / E2, x = idx - (idx / E2) * E2;
@@ -195,9 +217,6 @@ __global__ void __launch_bounds__(kStencilThreads, sizeof(T) == 4 ? 2 : 1) k_foe
   }
   __syncthreads();
 
-  const bool owner = tid < NB * NB;
-  const int oby = owner ? tid / NB : 0, obx = owner ? tid - (tid / NB) * NB : 0;
-  T outacc[4][4];
 #pragma unroll
   for (int yy = 0; yy < 4; ++yy)
 #pragma unroll
@@ -208,6 +227,8 @@ __global__ void __launch_bounds__(kStencilThreads, sizeof(T) == 4 ? 2 : 1) k_foe
         if (b <= 2 * rb) s = fma(g[b], h1[(4 * oby + yy + b) * VD + 4 * obx + xx], s);
       outacc[yy][xx] = T(2) * s + a.l2 * vs[(4 * oby + yy + kHalo) * VD + 4 * obx + xx + kHalo];
     }
+  }
+  __syncthreads();
 
   // ---- regulariser part: per filter z_j on the tile grown by R, then K_j^T z_j ----
   const int sby = tid >> 4, sbx = tid & 15;             // step-1 block of this thread
@@ -540,13 +561,22 @@ k_foe_jw(const PairDev* pairs, const TileDev* tiles, int n_tiles, const T* win, 
 // ---------------------------------------------------------------------------------------------
 // Direct (non-fused) kernels used by the TV regulariser and by the forward operator.
 
-// out = A in (minus y if y != null), zero boundary; one thread per pixel.
+// out = A in (minus y if y != null), zero boundary; one thread per pixel.  A: the pair's blur, or
+// the inpainting mask.
 template <typename T>
 __global__ void k_blur(const PairDev* pairs, const ChunkDev* chunks, const T* in, const T* y, T* out,
                        const int* mask) {
   const ChunkDev ch = chunks[blockIdx.x];
   if (mask && !mask[ch.pair]) return;
   const PairDev pr = pairs[ch.pair];
+  if (pr.opm) {   // inpainting: A = diag(mask)
+    for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
+      const long long pl = ch.start + t;
+      // unmeasured pixels carry no data: A x - y is zero there whatever y holds
+      out[pr.off + pl] = pr.opm[pl] ? (y ? in[pr.off + pl] - y[pr.off + pl] : in[pr.off + pl]) : T(0);
+    }
+    return;
+  }
   for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
     const long long pl = ch.start + t;
     const int i = (int)(pl / pr.w), j = (int)(pl - (pl / pr.w) * pr.w);

@@ -35,8 +35,9 @@ class StepInfo:
 class Engine:
     def __init__(self, problem: api.Problem, strategy="RGen-L(R)", s: int = 16, rtol: float = 1e-4,
                  lower_gtol: float = 1e-5, lower_max_iters: int = 5000, maxit: int = 5000,
-                 nsc_tol: Optional[float] = None, lower_relative: bool = True):
+                 nsc_tol: Optional[float] = None, lower_relative: bool = True, method: str = "cg"):
         self.P = problem
+        self.method = method            # "cg" (SPD Hessians) or "minres" (Algorithm 3, indefinite)
         self.strategy: Strategy = parse(strategy) if isinstance(strategy, str) else strategy
         self.s = s
         self.rtol = rtol
@@ -67,7 +68,7 @@ class Engine:
         scale = None if (not nsc or self.hg_prev is None) else [self.hg_prev] * self.P.K
         info = self.P.hessian_solve(self.w, g=g, recycle=st.recycles, nsc=nsc, tol=tol, relative=True,
                                     maxit=self.maxit, store_basis=st.recycles, warm_start=True, nsc_scale=scale,
-                                    allow_noconv=True)
+                                    allow_noconv=True, method=self.method)
         self.n_systems += 1
         mean, per, loss = self.P.hypergrad(self.w, per_pair=True, loss=True)
         self.hg_prev = float(mean.norm())

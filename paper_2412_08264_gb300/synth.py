@@ -5,7 +5,8 @@ noise realisations, blur widths and initial filter taps.  It holds none of
 the method's arithmetic (no blur, no regulariser, no solver), so that both
 the CUDA path and the FP64 checker can take their inputs from it without
 sharing any computation.  The measurement ``y = A x* + noise`` is formed by
-each side with its own blur.
+each side with its own operator (blur, or for inpainting the measured-pixel mask,
+which is drawn here as input data).
 
 Image model (piecewise-constant, Section 5 uses natural images; these are
 stand-ins of the same size): six axis-aligned rectangles with corners drawn
@@ -19,7 +20,7 @@ zero-mean once.  theta = [alpha_1, taps_1, ..., alpha_N, taps_N].
 from __future__ import annotations
 
 from dataclasses import dataclass, field
-from typing import List
+from typing import List, Optional
 
 import numpy as np
 
@@ -33,6 +34,7 @@ class PairSpec:
     blur_sigma: float
     blur_radius: int
     noise_sigma: float
+    keep: float = 0.0           # inpainting: fraction of measured pixels (0: blur operator)
 
 
 @dataclass
@@ -50,6 +52,7 @@ class Workload:
     precision: str = "fp32"     # "fp32" (FP32 stencils, FP64 reductions) or "fp64"
     x_star: List[np.ndarray] = field(default_factory=list)
     noise: List[np.ndarray] = field(default_factory=list)
+    masks: List[Optional[np.ndarray]] = field(default_factory=list)   # uint8 per pair, None: blur
     theta0: np.ndarray = None
 
     @property
@@ -79,6 +82,11 @@ def gaussian_noise(rng: np.random.Generator, h: int, w: int, sigma: float) -> np
     return sigma * rng.standard_normal((h, w))
 
 
+def keep_mask(rng: np.random.Generator, h: int, w: int, keep: float) -> np.ndarray:
+    """Random subsampling pattern: each pixel measured independently with probability `keep`."""
+    return (rng.random((h, w)) < keep).astype(np.uint8)
+
+
 def foe_theta_init(rng: np.random.Generator, n_filters: int, f: int,
                    alpha0: float = -3.0, std: float = 0.1) -> np.ndarray:
     theta = np.empty(n_filters * (f * f + 1), dtype=np.float64)
@@ -97,6 +105,7 @@ def _fill(wl: Workload, ss: np.random.SeedSequence) -> Workload:
         rng = np.random.default_rng(kid)
         wl.x_star.append(rectangles_image(rng, p.height, p.width))
         wl.noise.append(gaussian_noise(rng, p.height, p.width, p.noise_sigma))
+        wl.masks.append(keep_mask(rng, p.height, p.width, p.keep) if p.keep > 0 else None)
     rng = np.random.default_rng(kids[-1])
     if wl.reg == "tv":
         wl.theta0 = np.array([-3.0])
@@ -177,12 +186,23 @@ def uneven_foe(sizes, n_filters: int = 4, f: int = 5, blur_radius: int = 4, seed
     return _fill(wl, data_ss)
 
 
+def inpaint_batch(n_pairs: int = 1024, side: int = 28, keep: float = 0.3, noise_sigma: float = 0.1,
+                  n_filters: int = 3, f: int = 5, seed: int = 0) -> Workload:
+    """Inpainting pairs shaped like Section 5.1's experiment (28 x 28 images, 30 % of the pixels
+    measured, heavy noise, 3 learned 5 x 5 filters with phi = s^2), batched over many pairs."""
+    pairs = [PairSpec(side, side, 1.0, 0, noise_sigma, keep)] * n_pairs
+    wl = Workload(f"inpaint{n_pairs}x{side}_n{n_filters}f{f}", pairs, reg="foe", n_filters=n_filters,
+                  filter_size=f, phi="sq", recycle_dim=30)
+    return _fill(wl, np.random.SeedSequence([ROOT_SEED, 13, seed]))
+
+
 WORKLOADS = {
     "tv32_fp64": tv_32,
     "foe256_n8f5": foe_256,
     "batch64_foe_n16f5": batch_64,
     "batch8_1024_foe_n24f7": batch_1024,
     "large2048_foe_n48f7": large_2048,
+    "inpaint1024x28_n3f5": inpaint_batch,
 }
 
 
