@@ -36,6 +36,11 @@ INPAINT_RTOL = 1e-5
 LOWER_GTOL = 1e-5      # lower-level gradient tolerance (relative to ||grad Phi(0)||)
 ADAM_LR = 1e-2
 FP32_FMA_LANES = 152 * 128   # GB300: 152 SMs x 128 FP32 lanes
+# DRAM bytes (read + write) per pixel of one fused Hessian action with the recycled-CG dots over
+# 16 recycle columns, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum on the
+# first 16 pairs of the batch: 179.4 MB for 1,306,624 px; summary in
+# profiles/hvp_k_foe_stencil_f5_batch16.md), scaled to a launch by the pixels it processes.
+HVP_DRAM_BYTES_PER_PIXEL = 137.4
 
 
 def hvp_flops_per_pixel(n_filters, f, rb, masked=False):
@@ -175,7 +180,7 @@ def gpu_arm(args, rank, world, dist):
             info = P.hessian_solve(w, recycle=strat.recycles, nsc=strat.nsc, tol=rtol, relative=True, maxit=3000,
                                    store_basis=strat.recycles, warm_start=True,
                                    nsc_scale=None if hg_prev is None else [hg_prev] * K, allow_noconv=True,
-                                   method=args.method)
+                                   method=args.method, graph=args.graph)
             mean, per = P.hypergrad(w, per_pair=True)
             if world > 1:
                 mean = allreduce_mean(mean, K)
@@ -290,7 +295,8 @@ def oracle_sample(steps, warmup, max_seconds=None, strategy="RGen-L(R)", workloa
             Up = U if U is not None else np.zeros((ll.n, 0))
             U, C, Z, _ = refresh(Up, V, AH, lambda v: prob.Jw(0, x, theta, v), s_rec, st.kind, st.size, st.side)
         g = prob.rhs(0, x)
-        out = rcg(AH, g, w, U, C, tol=RTOL * np.linalg.norm(g), maxit=3000, kmax_store=MAX_BASIS)
+        out = rcg(AH, g, w, U, C, tol=(INPAINT_RTOL if workload == "inpaint" else RTOL) * np.linalg.norm(g),
+                  maxit=3000, kmax_store=MAX_BASIS)
         w, V = out["w"], out["V"]
         hg = prob.Jw(0, x, theta, w)
         theta = opt.step(theta, hg)
@@ -327,6 +333,9 @@ def main():
     ap.add_argument("--pairs", type=int, default=0, help="use only the first PAIRS pairs (profiling cases)")
     ap.add_argument("--prof-steps", type=int, default=2,
                     help="extra steps timed kernel by kernel with CUDA events (roofline, kernel_ms)")
+    ap.add_argument("--no-graph", dest="graph", action="store_false",
+                    help="launch the Krylov loop kernel by kernel from the host (profilers that do not "
+                         "follow conditional CUDA-graph bodies see every launch)")
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (ncu --profile-from-start off)")
     args = ap.parse_args()
@@ -383,10 +392,13 @@ def main():
     bpp = hvp_bytes_per_pixel(wl.n_filters, masked=masked)
     avg_ms = hv["ms"] / max(1, hv["launches"])
     flops_per_launch = fpp * hv["pixels"] / max(1, hv["launches"])
-    achieved_tflops = flops_per_launch / (avg_ms / 1e3) / 1e12
     ck = rec["clocks"] or {}
     peak_tflops = FP32_FMA_LANES * 2 * 2070e6 / 1e12
-    gbs = bpp * hv["pixels"] / max(1, hv["launches"]) / (avg_ms / 1e3) / 1e9
+    if avg_ms > 0:
+        achieved_tflops = flops_per_launch / (avg_ms / 1e3) / 1e12
+        gbs = bpp * hv["pixels"] / max(1, hv["launches"]) / (avg_ms / 1e3) / 1e9
+    else:   # no kernel-by-kernel pass (--prof-steps 0)
+        achieved_tflops = gbs = None
     line = {
         "metric": metric, "value": value, "unit": "hypergradients/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -400,7 +412,11 @@ def main():
         "krylov_iters_per_step": [int(np.max(it)) for it in rec["iters"]],
         "krylov_iters_total": int(np.sum(rec["iters"])),
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": peak_tflops, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / peak_tflops, "traffic": None,
+                     "frac": None if achieved_tflops is None else achieved_tflops / peak_tflops,
+                     "traffic": (HVP_DRAM_BYTES_PER_PIXEL * hv["pixels"] / max(1, hv["launches"])
+                                 if (hv["launches"] and not masked) else None),
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per pixel on the "
+                                       "16-pair case, scaled to the launch's pixels",
                      "kernel": "k_foe_stencil<float,5,HVP> (fused blur + FoE Hessian action + dots)",
                      "flops_per_pixel": fpp, "pixels_per_launch": hv["pixels"] / max(1, hv["launches"]),
                      "avg_launch_ms": avg_ms, "hbm_gbs_algorithmic": gbs,
