@@ -76,8 +76,10 @@ struct SolveState {
 // `hist_head` (the next slot written) never holds one of them.
 struct LbfgsState {
   double f, f_trial, gtd, t, gnorm, gtol, gamma;
-  int active, accepted, iters, status, hist_count, hist_head, backtracks, pad;
+  int active, accepted, iters, status, hist_count, hist_head, backtracks;
+  int phase;   // kLbDir: needs a direction; kLbTrial: line search running; kLbAccepted: step to take
 };
+constexpr int kLbDir = 0, kLbTrial = 1, kLbAccepted = 2;
 
 struct ProfEvent {
   cudaEvent_t a, b;
@@ -92,6 +94,16 @@ struct KrylovGraphKey {
   bool operator==(const KrylovGraphKey& o) const {
     return fused == o.fused && store == o.store && nsc == o.nsc && minres == o.minres && tpart == o.tpart &&
            cpart == o.cpart && V == o.V;
+  }
+};
+// The L-BFGS loop as one graph launch: its body bakes these options into its kernels.
+struct LbfgsGraphKey {
+  const void *cpart, *tpart, *S;
+  int MH, max_bt, maxit;
+  double slack;
+  bool operator==(const LbfgsGraphKey& o) const {
+    return cpart == o.cpart && tpart == o.tpart && S == o.S && MH == o.MH && max_bt == o.max_bt && maxit == o.maxit &&
+           slack == o.slack;
   }
 };
 struct KrylovGraph {
@@ -158,6 +170,8 @@ struct bl_problem {
   int* d_loop = nullptr;    // graph loop counter and cap
   cudaStream_t cstream = nullptr;   // private stream used only to capture graphs
   bl::KrylovGraph* kgraph = nullptr;
+  bl::KrylovGraph* lgraph = nullptr;     // the L-BFGS loop (its key: lgraph_key)
+  bl::LbfgsGraphKey lgraph_key{};
   bool graph_failed = false;        // graph capture unavailable: the stream path is used
   bool graph_used = false;          // the last solve ran as a graph launch
   bool capturing = false;           // a graph capture is recording the launches
@@ -236,7 +250,8 @@ bl_status run_hessian_solve(bl_problem* P, const int* mask_host, const bl_krylov
                             const void* g_batched, const double* nsc_scale_batched,
                             std::vector<bl_solve_info>& info);
 
-void destroy_krylov_graph(bl_problem* P);
+void destroy_krylov_graph(bl_problem* P);   // also drops the L-BFGS loop graph
+void destroy_lbfgs_graph(bl_problem* P);
 
 // ---- recycle.cu ----
 bl_status run_ritz_update(bl_problem* P, const std::vector<int>& mask_host,

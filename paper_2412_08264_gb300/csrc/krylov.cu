@@ -706,6 +706,7 @@ static bl_status build_krylov_graph(bl_problem* P, const KrylovGraphKey& key, F&
 }
 
 void destroy_krylov_graph(bl_problem* P) {
+  destroy_lbfgs_graph(P);
   if (!P->kgraph) return;
   if (P->kgraph->exec) cudaGraphExecDestroy(P->kgraph->exec);
   if (P->kgraph->graph) cudaGraphDestroy(P->kgraph->graph);

@@ -43,7 +43,7 @@ __global__ void k_lb_dots(LbArgs a, const T* g, const T* Sm, const T* Ym, double
   __shared__ double red[8][4 * (kMaxHistory + 1)];
   const ChunkDev ch = a.chunks[blockIdx.x];
   const LbfgsState S = a.st[ch.pair];
-  if (!S.active || S.hist_count == 0) return;
+  if (!S.active || S.phase != kLbDir || S.hist_count == 0) return;
   const PairDev pr = a.pairs[ch.pair];
   const int RS = a.MH + 1, c = S.hist_count;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -83,7 +83,7 @@ __global__ void k_lb_compact(LbArgs a, const double* part) {
   __shared__ double v[4 * (kMaxHistory + 1)];
   const int k = blockIdx.x;
   const LbfgsState S = a.st[k];
-  if (!S.active) return;
+  if (!S.active || S.phase != kLbDir) return;
   const PairDev pr = a.pairs[k];
   const int RS = a.MH + 1, c = S.hist_count;
   for (int q = threadIdx.x; q < 4 * c; q += blockDim.x) {
@@ -144,7 +144,7 @@ __global__ void k_lb_dir(LbArgs a, T* d, const T* g, const T* Sm, const T* Ym, d
   __shared__ int sl[kMaxHistory + 1];
   const ChunkDev ch = a.chunks[blockIdx.x];
   const LbfgsState S = a.st[ch.pair];
-  if (!S.active) return;
+  if (!S.active || S.phase != kLbDir) return;
   const PairDev pr = a.pairs[ch.pair];
   const int RS = a.MH + 1, c = S.hist_count;
   if ((int)threadIdx.x < c) {
@@ -175,7 +175,7 @@ __global__ void k_lb_dir(LbArgs a, T* d, const T* g, const T* Sm, const T* Ym, d
 __global__ void k_lb_gtd(LbArgs a, const double* part) {
   const int k = blockIdx.x;
   LbfgsState& S = a.st[k];
-  if (!S.active || threadIdx.x != 0) return;
+  if (!S.active || S.phase != kLbDir || threadIdx.x != 0) return;
   const PairDev pr = a.pairs[k];
   double sum = 0.0;
   for (int u = pr.cbeg; u < pr.cend; ++u) sum += part[u];
@@ -189,7 +189,7 @@ __global__ void k_lb_restart(LbArgs a, T* d, const T* g) {
   __shared__ double red[40];
   const ChunkDev ch = a.chunks[blockIdx.x];
   const LbfgsState S = a.st[ch.pair];
-  if (!S.active || S.accepted != -1) return;
+  if (!S.active || S.phase != kLbDir || S.accepted != -1) return;
   const PairDev pr = a.pairs[ch.pair];
   Accum<T> acc;
   for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
@@ -204,7 +204,7 @@ __global__ void k_lb_restart(LbArgs a, T* d, const T* g) {
 __global__ void k_lb_restart_fix(LbArgs a) {
   const int k = blockIdx.x;
   LbfgsState& S = a.st[k];
-  if (!S.active || threadIdx.x != 0 || S.accepted != -1) return;
+  if (!S.active || S.phase != kLbDir || threadIdx.x != 0 || S.accepted != -1) return;
   const PairDev pr = a.pairs[k];
   double sum = 0.0;
   for (int u = pr.cbeg; u < pr.cend; ++u) sum += a.cpart[u];
@@ -213,16 +213,18 @@ __global__ void k_lb_restart_fix(LbArgs a) {
   S.accepted = 0;
 }
 
+// pairs with a new direction start their line search at t = 1; pairs still searching continue
 __global__ void k_lb_begin_search(LbArgs a, int* search_mask) {
   const int k = blockIdx.x;
   LbfgsState& S = a.st[k];
   if (threadIdx.x != 0) return;
-  if (S.active) {
+  if (S.active && S.phase == kLbDir) {
     S.t = 1.0;
     S.backtracks = 0;
     S.accepted = 0;
+    S.phase = kLbTrial;
   }
-  search_mask[k] = S.active;
+  search_mask[k] = S.active && S.phase == kLbTrial;
 }
 
 // x_t = x + t d for searching pairs
@@ -249,11 +251,12 @@ __global__ void k_lb_armijo(LbArgs a, int* search_mask, const double* vals, doub
   if (ft <= S.f + 1e-4 * S.t * S.gtd + slack * fabs(S.f) || S.backtracks + 1 >= max_bt) {
     S.f_trial = ft;
     S.accepted = 1;
+    S.phase = kLbAccepted;
     search_mask[k] = 0;
   } else {
     S.t *= 0.5;
     S.backtracks += 1;
-    atomicAdd(flag, 1);
+    if (flag) atomicAdd(flag, 1);
   }
 }
 
@@ -263,7 +266,7 @@ __global__ void k_lb_accept(LbArgs a, T* x, T* g, const T* xt, const T* gt, T* S
   __shared__ double red[40];
   const ChunkDev ch = a.chunks[blockIdx.x];
   const LbfgsState S = a.st[ch.pair];
-  if (!S.active) return;
+  if (!S.active || S.phase != kLbAccepted) return;
   const PairDev pr = a.pairs[ch.pair];
   T* sc = Sm + pr.off * (a.MH + 1) + (long long)S.hist_head * pr.n;
   T* yc = Ym + pr.off * (a.MH + 1) + (long long)S.hist_head * pr.n;
@@ -293,32 +296,36 @@ __global__ void k_lb_accept(LbArgs a, T* x, T* g, const T* xt, const T* gt, T* S
   }
 }
 
+// take the accepted steps (history, scaling, convergence test); count the pairs still running
 __global__ void k_lb_post(LbArgs a, int maxit, int* flag) {
   const int k = blockIdx.x;
   LbfgsState& S = a.st[k];
   if (!S.active || threadIdx.x != 0) return;
-  const PairDev pr = a.pairs[k];
-  double v[4] = {0, 0, 0, 0};
-  for (int u = pr.cbeg; u < pr.cend; ++u)
-    for (int c = 0; c < 4; ++c) v[c] += a.cpart[(size_t)u * 4 + c];
-  const double sy = v[0], yy = v[1], ss = v[2], gg = v[3];
-  if (sy > 1e-12 * sqrt(ss) * sqrt(yy)) {
-    S.gamma = sy / yy;
-    S.hist_head = (S.hist_head + 1) % (a.MH + 1);
-    S.hist_count = min(S.hist_count + 1, a.MH);
-  }
-  if (S.hist_count == 0) S.gamma = 1.0;
-  S.f = S.f_trial;
-  S.gnorm = sqrt(gg);
-  S.iters += 1;
-  if (!isfinite(S.f) || !isfinite(S.gnorm)) {
-    S.active = 0;
-    S.status = BL_EBREAKDOWN;
-  } else if (S.gnorm <= S.gtol) {
-    S.active = 0;
-  } else if (S.iters >= maxit) {
-    S.active = 0;
-    S.status = BL_ENOCONV;
+  if (S.phase == kLbAccepted) {
+    const PairDev pr = a.pairs[k];
+    double v[4] = {0, 0, 0, 0};
+    for (int u = pr.cbeg; u < pr.cend; ++u)
+      for (int c = 0; c < 4; ++c) v[c] += a.cpart[(size_t)u * 4 + c];
+    const double sy = v[0], yy = v[1], ss = v[2], gg = v[3];
+    if (sy > 1e-12 * sqrt(ss) * sqrt(yy)) {
+      S.gamma = sy / yy;
+      S.hist_head = (S.hist_head + 1) % (a.MH + 1);
+      S.hist_count = min(S.hist_count + 1, a.MH);
+    }
+    if (S.hist_count == 0) S.gamma = 1.0;
+    S.f = S.f_trial;
+    S.gnorm = sqrt(gg);
+    S.iters += 1;
+    S.phase = kLbDir;
+    if (!isfinite(S.f) || !isfinite(S.gnorm)) {
+      S.active = 0;
+      S.status = BL_EBREAKDOWN;
+    } else if (S.gnorm <= S.gtol) {
+      S.active = 0;
+    } else if (S.iters >= maxit) {
+      S.active = 0;
+      S.status = BL_ENOCONV;
+    }
   }
   if (S.active) atomicAdd(flag, 1);
 }
@@ -340,6 +347,7 @@ __global__ void k_lb_init(LbArgs a, const int* mask, const double* vals, const d
   S.gamma = 1.0;
   S.iters = 0;
   S.status = BL_OK;
+  S.phase = kLbDir;
   S.active = (S.gnorm > S.gtol) ? 1 : 0;
   if (!isfinite(S.f) || !isfinite(S.gnorm)) {
     S.active = 0;
@@ -350,6 +358,68 @@ __global__ void k_lb_init(LbArgs a, const int* mask, const double* vals, const d
 
 __global__ void k_lb_mask(const LbfgsState* st, int* out, int K) {
   for (int k = threadIdx.x; k < K; k += blockDim.x) out[k] = st[k].active;
+}
+
+// WHILE-node condition of the L-BFGS loop: another body run while some pair is active and the
+// run cap is not reached.
+__global__ void k_lb_loop_cond(cudaGraphConditionalHandle h, const int* flag, int* loop) {
+  const int ran = ++loop[0];
+  cudaGraphSetConditional(h, (*flag > 0 && ran < loop[1]) ? 1u : 0u);
+}
+
+template <typename F>
+static bl_status build_lbfgs_graph(bl_problem* P, const LbfgsGraphKey& key, F&& body) {
+  destroy_lbfgs_graph(P);
+  if (!P->cstream) BL_CUDA_TRY(cudaStreamCreateWithFlags(&P->cstream, cudaStreamNonBlocking));
+  KrylovGraph* G = new KrylovGraph();
+  P->lgraph = G;
+  P->lgraph_key = key;
+  BL_CUDA_TRY(cudaGraphCreate(&G->graph, 0));
+  cudaGraphConditionalHandle h;
+  BL_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, G->graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  BL_CUDA_TRY(cudaGraphAddNode(&node, G->graph, nullptr, nullptr, 0, &cp));
+  cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
+  // capture one body run on a private stream (capture only records)
+  cudaStream_t user = P->stream;
+  const bool prof = P->prof;
+  const int64_t l0 = P->launches;
+  P->stream = P->cstream;
+  P->prof = false;
+  P->capturing = true;
+  bl_status st = BL_OK;
+  cudaError_t e = cudaStreamBeginCaptureToGraph(P->stream, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+  if (e == cudaSuccess) {
+    st = body();
+    if (st == BL_OK) {
+      k_lb_loop_cond<<<1, 1, 0, P->stream>>>(h, P->d_flag, P->d_loop);
+      ++P->launches;
+      e = cudaGetLastError();
+    }
+    cudaGraph_t out = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(P->stream, &out);
+    if (e == cudaSuccess) e = e2;
+  }
+  G->body_kernels = (int)(P->launches - l0);
+  P->launches = l0;
+  P->stream = user;
+  P->prof = prof;
+  P->capturing = false;
+  if (st != BL_OK) {
+    destroy_lbfgs_graph(P);
+    return st;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&G->exec, G->graph, 0);
+  if (e != cudaSuccess) {
+    destroy_lbfgs_graph(P);
+    return fail(BL_ECUDA, std::string("L-BFGS graph: ") + cudaGetErrorString(e));
+  }
+  return BL_OK;
 }
 
 template <typename T>
@@ -399,58 +469,73 @@ static bl_status lbfgs_impl(bl_problem* P, const std::vector<int>& mask_host, co
   BL_LAUNCH_CHECK(P);
   BL_CUDA_TRY(cudaMemcpyAsync(P->h_flag, P->d_flag, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
   BL_CUDA_TRY(cudaStreamSynchronize(P->stream));
-  int hist = 0;   // upper bound on any pair's history count
-  for (int it = 0; it < o->max_iters && *P->h_flag > 0; ++it) {
-    // ---- direction d = -H g (compact representation) ----
-    {
-    ProfScope ps(P, BL_KC_LBFGS);
-    if (hist > 0) {
-      k_lb_dots<T><<<cg, ct, 0, P->stream>>>(a, g, Sm, Ym, P->cpart);
-      BL_LAUNCH_CHECK(P);
-    }
-    k_lb_compact<<<K, 32, 0, P->stream>>>(a, P->cpart);
-    BL_LAUNCH_CHECK(P);
-    double* pd = P->cpart + (size_t)P->n_chunks * 4 * (MH + 1);
-    k_lb_dir<T><<<cg, ct, 0, P->stream>>>(a, d, g, Sm, Ym, pd);
-    BL_LAUNCH_CHECK(P);
-    k_lb_gtd<<<K, 32, 0, P->stream>>>(a, pd);
-    BL_LAUNCH_CHECK(P);
-    k_lb_restart<T><<<cg, ct, 0, P->stream>>>(a, d, g);
-    BL_LAUNCH_CHECK(P);
-    k_lb_restart_fix<<<K, 32, 0, P->stream>>>(a);
-    BL_LAUNCH_CHECK(P);
-    // ---- backtracking ----
-    k_lb_begin_search<<<K, 32, 0, P->stream>>>(a, smask);
-    BL_LAUNCH_CHECK(P);
-    }
-    for (int bt = 0; bt < std::max(1, o->max_backtrack); ++bt) {
-      {
-        ProfScope ps(P, BL_KC_LBFGS);
-        k_lb_trial<T><<<cg, ct, 0, P->stream>>>(a, smask, xt, x, d);
-        BL_LAUNCH_CHECK(P);
-      }
-      st = launch_grad(P, xt, gt, smask, vals);
-      if (st != BL_OK) return st;
-      BL_CUDA_TRY(cudaMemsetAsync(P->d_flag, 0, sizeof(int), P->stream));
-      k_lb_armijo<<<K, 32, 0, P->stream>>>(a, smask, vals, l2, std::max(1, o->max_backtrack), o->armijo_slack,
-                                            P->d_flag);
-      BL_LAUNCH_CHECK(P);
-      BL_CUDA_TRY(cudaMemcpyAsync(P->h_flag, P->d_flag, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
-      BL_CUDA_TRY(cudaStreamSynchronize(P->stream));
-      if (*P->h_flag == 0) break;
-    }
-    // ---- accept ----
+  // One body run advances every active pair by one phase: pairs needing a direction get one and
+  // take their first trial point; pairs still searching take their next (halved) trial point;
+  // accepted steps update x, g and the history.  Each pair follows exactly the sequential
+  // algorithm; pairs only drift apart in how many body runs their backtracking takes.
+  const int max_bt = std::max(1, o->max_backtrack);
+  auto body = [&]() -> bl_status {
     {
       ProfScope ps(P, BL_KC_LBFGS);
-      k_lb_accept<T><<<cg, ct, 0, P->stream>>>(a, x, g, xt, gt, Sm, Ym);
+      k_lb_dots<T><<<cg, ct, 0, P->stream>>>(a, g, Sm, Ym, P->cpart);
       BL_LAUNCH_CHECK(P);
-      BL_CUDA_TRY(cudaMemsetAsync(P->d_flag, 0, sizeof(int), P->stream));
-      k_lb_post<<<K, 32, 0, P->stream>>>(a, o->max_iters, P->d_flag);
+      k_lb_compact<<<K, 32, 0, P->stream>>>(a, P->cpart);
+      BL_LAUNCH_CHECK(P);
+      double* pd = P->cpart + (size_t)P->n_chunks * 4 * (MH + 1);
+      k_lb_dir<T><<<cg, ct, 0, P->stream>>>(a, d, g, Sm, Ym, pd);
+      BL_LAUNCH_CHECK(P);
+      k_lb_gtd<<<K, 32, 0, P->stream>>>(a, pd);
+      BL_LAUNCH_CHECK(P);
+      k_lb_restart<T><<<cg, ct, 0, P->stream>>>(a, d, g);
+      BL_LAUNCH_CHECK(P);
+      k_lb_restart_fix<<<K, 32, 0, P->stream>>>(a);
+      BL_LAUNCH_CHECK(P);
+      k_lb_begin_search<<<K, 32, 0, P->stream>>>(a, smask);
+      BL_LAUNCH_CHECK(P);
+      k_lb_trial<T><<<cg, ct, 0, P->stream>>>(a, smask, xt, x, d);
       BL_LAUNCH_CHECK(P);
     }
-    BL_CUDA_TRY(cudaMemcpyAsync(P->h_flag, P->d_flag, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+    bl_status s2 = launch_grad(P, xt, gt, smask, vals);
+    if (s2 != BL_OK) return s2;
+    ProfScope ps(P, BL_KC_LBFGS);
+    k_lb_armijo<<<K, 32, 0, P->stream>>>(a, smask, vals, l2, max_bt, o->armijo_slack, nullptr);
+    BL_LAUNCH_CHECK(P);
+    k_lb_accept<T><<<cg, ct, 0, P->stream>>>(a, x, g, xt, gt, Sm, Ym);
+    BL_LAUNCH_CHECK(P);
+    BL_CUDA_TRY(cudaMemsetAsync(P->d_flag, 0, sizeof(int), P->stream));
+    k_lb_post<<<K, 32, 0, P->stream>>>(a, o->max_iters, P->d_flag);
+    BL_LAUNCH_CHECK(P);
+    return BL_OK;
+  };
+  // every accepted step takes at most max_bt body runs
+  const long long cap = (long long)o->max_iters * max_bt + 1;
+  bool use_graph = *P->h_flag > 0 && !P->prof && !P->graph_failed;
+  if (use_graph) {
+    const LbfgsGraphKey key{P->cpart, P->tpart, P->S, MH, max_bt, o->max_iters, o->armijo_slack};
+    if (!P->lgraph || !(P->lgraph_key == key)) {
+      if (build_lbfgs_graph(P, key, body) != BL_OK) {
+        P->graph_error = error_copy();
+        P->graph_failed = true;
+        use_graph = false;
+        (void)cudaGetLastError();
+      }
+    }
+  }
+  if (use_graph) {
+    const int capi[2] = {0, (int)std::min<long long>(cap, 1 << 30)};
+    BL_CUDA_TRY(cudaMemcpyAsync(P->d_loop, capi, sizeof(capi), cudaMemcpyHostToDevice, P->stream));
+    BL_CUDA_TRY(cudaGraphLaunch(P->lgraph->exec, P->stream));
+    int ran = 0;
+    BL_CUDA_TRY(cudaMemcpyAsync(&ran, P->d_loop, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
     BL_CUDA_TRY(cudaStreamSynchronize(P->stream));
-    hist = std::min(hist + 1, MH);
+    P->launches += (int64_t)ran * P->lgraph->body_kernels + 1;
+  } else {
+    for (long long run = 0; run < cap && *P->h_flag > 0; ++run) {
+      st = body();
+      if (st != BL_OK) return st;
+      BL_CUDA_TRY(cudaMemcpyAsync(P->h_flag, P->d_flag, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+      BL_CUDA_TRY(cudaStreamSynchronize(P->stream));
+    }
   }
   std::vector<LbfgsState> hs(K);
   BL_CUDA_TRY(cudaMemcpyAsync(hs.data(), P->lst, K * sizeof(LbfgsState), cudaMemcpyDeviceToHost, P->stream));
@@ -465,6 +550,14 @@ static bl_status lbfgs_impl(bl_problem* P, const std::vector<int>& mask_host, co
     info[k].rhs_norm = hs[k].gtol;
   }
   return BL_OK;
+}
+
+void destroy_lbfgs_graph(bl_problem* P) {
+  if (!P->lgraph) return;
+  if (P->lgraph->exec) cudaGraphExecDestroy(P->lgraph->exec);
+  if (P->lgraph->graph) cudaGraphDestroy(P->lgraph->graph);
+  delete P->lgraph;
+  P->lgraph = nullptr;
 }
 
 bl_status run_lower_solve(bl_problem* P, const std::vector<int>& mask_host, const bl_lbfgs_opts* o,

@@ -61,6 +61,7 @@ std::vector<int> host_mask(const bl_problem* P, const int32_t* pairs, int32_t np
 
 bl_status ensure_history(bl_problem* P, int m) {
   if (m == P->MH && P->S) return BL_OK;
+  destroy_lbfgs_graph(P);
   if (P->S) {
     cudaStreamSynchronize(P->stream);
     for (void* b : {(void*)P->S, (void*)P->Yh, (void*)P->lsy, (void*)P->lyy, (void*)P->lcs, (void*)P->lcy})

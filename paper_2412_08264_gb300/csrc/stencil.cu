@@ -431,12 +431,22 @@ __global__ void k_fields(const PairDev* pairs, const ChunkDev* chunks, const T* 
 //   (J w)_{alpha_j}  = -e^{alpha_j} sum_p e_p (k_j * w)_p
 //   (J w)_{k_j[o]}   = -e^{alpha_j} sum_p [ e_p w_{p+o} + phi''(u_p) (k_j * w)_p x^_{p+o} ]
 // Tile partials: tpart[((col * n_tiles) + tile) * p + m].
+// Row pitch of the staged w and x^ tiles of the J w kernel.  FP32: a multiple of 4 floats with an
+// odd number of 16-byte units, so the 128-bit row-segment reads of the lanes of a warp (consecutive
+// 4-pixel blocks, several block rows) fall in distinct bank groups.  FP64 keeps the plain side
+// (its scalar reads gain nothing, and the 7x7 FP64 tile needs the shared memory).
+template <typename T>
+__host__ __device__ constexpr int jw_pitch(int rs) {
+  return sizeof(T) != 4 ? rs : (((rs + 3) / 4) % 2 == 1 ? ((rs + 3) / 4) * 4 : ((rs + 3) / 4) * 4 + 4);
+}
+
 template <typename T, int F>
 __global__ void __launch_bounds__(kStencilThreads, sizeof(T) == 4 ? 2 : 1)
 k_foe_jw(const PairDev* pairs, const TileDev* tiles, int n_tiles, const T* win, int mult,
          const int* cols, const T* xhat, const T* fu, const T* taps, const double* ealpha, int N,
          T eps, int phi, long long n_tot, const int* mask, double* tpart, int p, unsigned long long* pix) {
   constexpr int R = F / 2, TILE = tile_out(F), RS = TILE + 2 * R;   // staged region side
+  constexpr int RP = jw_pitch<T>(RS);                                 // its row pitch
   constexpr int NB = TILE / 4, FF = F * F;
   const TileDev tl = tiles[blockIdx.x];
   const PairDev pr = pairs[tl.pair];
@@ -447,18 +457,18 @@ k_foe_jw(const PairDev* pairs, const TileDev* tiles, int n_tiles, const T* win, 
     atomicAdd(pix, (unsigned long long)(min(TILE, pr.h - tl.oy) * min(TILE, pr.w - tl.ox)));
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* ws = reinterpret_cast<T*>(smem_raw);
-  T* xs = ws + RS * RS;
-  T* fbuf = xs + RS * RS;                                             // 2 x 16 x 256 prefetched u_j
+  T* xs = ws + RS * RP;
+  T* fbuf = xs + RS * RP;                                             // 2 x 16 x 256 prefetched u_j
   T* rf = fbuf + 2 * 16 * kStencilThreads;                            // (FF + 1) x 256 per-thread sums
   const int tid = threadIdx.x, lane = tid & 31;
   const T* wv = col_ptr(win, pr, mult, col);
-  constexpr bool kAligned = RS % 4 == 0;
+  constexpr bool kAligned = RP % 4 == 0;
   for (int idx = tid; idx < RS * RS; idx += kStencilThreads) {
     const int i = idx / RS, j = idx - (idx / RS) * RS;
     const int iy = tl.oy - R + i, ix = tl.ox - R + j;
     const bool in = iy >= 0 && iy < pr.h && ix >= 0 && ix < pr.w;
-    ws[idx] = in ? wv[(long long)iy * pr.w + ix] : T(0);
-    xs[idx] = in ? xhat[pr.off + (long long)iy * pr.w + ix] : T(0);
+    ws[i * RP + j] = in ? wv[(long long)iy * pr.w + ix] : T(0);
+    xs[i * RP + j] = in ? xhat[pr.off + (long long)iy * pr.w + ix] : T(0);
   }
   __syncthreads();
   const bool owner = tid < NB * NB;
@@ -491,7 +501,7 @@ k_foe_jw(const PairDev* pairs, const TileDev* tiles, int n_tiles, const T* win, 
     for (int yy = 0; yy < 4; ++yy)
 #pragma unroll
       for (int xx = 0; xx < 4; ++xx) kw[yy][xx] = 0;
-    corr_block<F, 4, 4, false, kAligned>(&ws[(4 * oby) * RS + 4 * obx], RS, k, kw);
+    corr_block<F, 4, 4, false, kAligned>(&ws[(4 * oby) * RP + 4 * obx], RP, k, kw);
     cp_async_wait_prev();
     T ga = 0;
 #pragma unroll
@@ -516,10 +526,21 @@ k_foe_jw(const PairDev* pairs, const TileDev* tiles, int n_tiles, const T* win, 
 #pragma unroll
     for (int ry = 0; ry < 4 + F - 1; ++ry) {
       T wseg[4 + F - 1], xseg[4 + F - 1];
+      const int rbase = (4 * oby + ry) * RP + 4 * obx;
+      if constexpr (sizeof(T) == 4 && (4 + F - 1) % 4 == 0) {
 #pragma unroll
-      for (int c = 0; c < 4 + F - 1; ++c) {
-        wseg[c] = ws[(4 * oby + ry) * RS + 4 * obx + c];
-        xseg[c] = xs[(4 * oby + ry) * RS + 4 * obx + c];
+        for (int c = 0; c < 4 + F - 1; c += 4) {
+          const float4 wv4 = *reinterpret_cast<const float4*>(&ws[rbase + c]);
+          const float4 xv4 = *reinterpret_cast<const float4*>(&xs[rbase + c]);
+          wseg[c] = wv4.x; wseg[c + 1] = wv4.y; wseg[c + 2] = wv4.z; wseg[c + 3] = wv4.w;
+          xseg[c] = xv4.x; xseg[c + 1] = xv4.y; xseg[c + 2] = xv4.z; xseg[c + 3] = xv4.w;
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4 + F - 1; ++c) {
+          wseg[c] = ws[rbase + c];
+          xseg[c] = xs[rbase + c];
+        }
       }
 #pragma unroll
       for (int yy = 0; yy < 4; ++yy) {
@@ -969,7 +990,7 @@ static bl_status jw_impl(bl_problem* P, const void* in, int mult, int cols, cons
 #define BL_JW_CASE(FF)                                                                            \
   case FF: {                                                                                      \
     constexpr int RS = tile_out(FF) + 2 * (FF / 2);                                               \
-    size_t sm = (2 * (size_t)RS * RS + 2 * 16 * kStencilThreads +                                 \
+    size_t sm = (2 * (size_t)RS * jw_pitch<T>(RS) + 2 * 16 * kStencilThreads +                    \
                  (size_t)(FF * FF + 1) * kStencilThreads) * sizeof(T);                            \
     if (!P->capturing)                                                                            \
       BL_CUDA_TRY(cudaFuncSetAttribute(k_foe_jw<T, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, \

@@ -154,6 +154,24 @@ def test_lower_solve_trajectory_fp64_matches_checker():
             assert abs(info[k]["value"] - out["f"]) <= 1e-10 * abs(out["f"])
 
 
+def test_lower_solve_graph_matches_stream():
+    """The L-BFGS loop launched as one CUDA graph gives the host-polled loop's iterations and
+    bit-identical iterates (the host-polled loop runs while profiling is enabled)."""
+    wl = small_wl(sizes=((64, 70), (33, 40), (90, 31)), N=3, seed=23)
+    P, prob, dt = make(wl, "fp32")
+    theta = torch.tensor(r32(wl.theta0), dtype=torch.float64, device=DEV)
+    outs = []
+    for prof in (True, False, False):
+        P.profile(prof)
+        x = P.zeros()
+        info = P.lower_solve(theta, x, gtol=1e-5, relative=True, max_iters=500, history=6)
+        outs.append(([d["iters"] for d in info], [d["value"] for d in info], x.cpu().numpy()))
+    P.profile(False)
+    assert outs[0][0] == outs[1][0] == outs[2][0]
+    assert outs[0][1] == outs[1][1] == outs[2][1]
+    assert np.array_equal(outs[0][2], outs[1][2]) and np.array_equal(outs[1][2], outs[2][2])
+
+
 def test_full_hypergradient_fp32():
     """Lower solve, Hessian solve and J w on the GPU (FP32) against the checker's reference."""
     wl = small_wl(sizes=((56, 56), (40, 72)), N=4, seed=11)
