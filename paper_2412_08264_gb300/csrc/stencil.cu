@@ -244,16 +244,27 @@ __global__ void __launch_bounds__(kStencilThreads, sizeof(T) == 4 ? 2 : 1) k_foe
                        oy - R + 4 * sby + 3 >= 0 && ox - R + 4 * sbx + 3 >= 0;
   const bool s2_live = owner && oy + 4 * oby < h && ox + 4 * obx < w;
   __syncthreads();                                      // every thread is done with h1 / av
+  // which of the block's 16 field values lie in the image (fixed over the filters), and the
+  // offset of its top-left pixel in one field; filter jf adds jf * n_tot
+  unsigned fmask = 0;
+#pragma unroll
+  for (int yy = 0; yy < 4; ++yy)
+#pragma unroll
+    for (int xx = 0; xx < 4; ++xx) {
+      const int ey = 4 * sby + yy, ex = 4 * sbx + xx;
+      const int iy = oy - R + ey, ix = ox - R + ex;
+      if (ey < E1 && ex < E1 && iy >= 0 && iy < h && ix >= 0 && ix < w) fmask |= 1u << (yy * 4 + xx);
+    }
+  const long long fofs = pr.off + (long long)(oy - R + 4 * sby) * w + (ox - R + 4 * sbx);
   auto prefetch = [&](int jf, int buf) {
+    const T* fb = a.fd + (long long)jf * a.n_tot + fofs;
 #pragma unroll
     for (int yy = 0; yy < 4; ++yy)
 #pragma unroll
       for (int xx = 0; xx < 4; ++xx) {
-        const int ey = 4 * sby + yy, ex = 4 * sbx + xx;
-        const int iy = oy - R + ey, ix = ox - R + ex;
         T* dst = &dbuf[(buf * 16 + yy * 4 + xx) * kStencilThreads + tid];
-        if (ey < E1 && ex < E1 && iy >= 0 && iy < h && ix >= 0 && ix < w)
-          cp_async_elem(dst, &a.fd[(long long)jf * a.n_tot + pr.off + (long long)iy * w + ix]);
+        if (fmask & (1u << (yy * 4 + xx)))
+          cp_async_elem(dst, fb + yy * w + xx);
         else
           *dst = T(0);
       }
