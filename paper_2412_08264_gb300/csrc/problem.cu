@@ -609,14 +609,17 @@ bl_status bl_recycle_export(bl_problem* P, int32_t pair, void* buf, size_t* byte
   const size_t base = (size_t)ph.off * P->SMAX * P->esz;
   BL_CUDA_TRY(cudaMemcpyAsync(o, (const char*)P->U + base, vec, cudaMemcpyDeviceToHost, P->stream));
   BL_CUDA_TRY(cudaMemcpyAsync(o + vec, (const char*)P->C + base, vec, cudaMemcpyDeviceToHost, P->stream));
-  BL_CUDA_TRY(cudaMemcpyAsync(o + 2 * vec, (const char*)P->Z + base, vec, cudaMemcpyDeviceToHost, P->stream));
+  if (P->hz_k[pair])
+    BL_CUDA_TRY(cudaMemcpyAsync(o + 2 * vec, (const char*)P->Z + base, vec, cudaMemcpyDeviceToHost, P->stream));
+  else
+    memset(o + 2 * vec, 0, vec);   // no Ritz-GSV operator for this pair: Z is written as zeros
   std::vector<double> ztc((size_t)P->SMAX * P->SMAX);
   BL_CUDA_TRY(cudaMemcpyAsync(ztc.data(), P->ztc + (size_t)pair * P->SMAX * P->SMAX, ztc.size() * sizeof(double),
                               cudaMemcpyDeviceToHost, P->stream));
   BL_CUDA_TRY(cudaStreamSynchronize(P->stream));
   double* zo = (double*)(o + 3 * vec);
   for (int i = 0; i < s; ++i)
-    for (int j = 0; j < s; ++j) zo[i * s + j] = ztc[(size_t)i * P->SMAX + j];
+    for (int j = 0; j < s; ++j) zo[i * s + j] = P->hz_k[pair] ? ztc[(size_t)i * P->SMAX + j] : 0.0;
   *bytes = need;
   return BL_OK;
 }

@@ -42,7 +42,7 @@ def test_minres_plain_matches_checker_fp64():
     wl = small_wl()
     P, prob, dt = make(wl, "fp64", max_recycle=4, max_basis=60)
     th = wl.theta0
-    xs, _ = prob.solve_lower(th, gtol=1e-10)
+    xs, _ = prob.solve_lower(th, gtol=1e-8)
     P.set_point(torch.tensor(th, dtype=torch.float64, device=DEV), packed(xs, dt))
     w = P.zeros()
     info = P.hessian_solve(w, recycle=False, tol=1e-8, relative=True, maxit=3000, method="minres", warm_start=False)
@@ -94,7 +94,7 @@ def test_rminres_sequence_fp64_matches_checker():
     V = None
     w_prev = None
     for i in range(3):
-        xs, _ = prob.solve_lower(th, gtol=1e-10)
+        xs, _ = prob.solve_lower(th, gtol=1e-8)
         x = xs[0]
         P.set_point(torch.tensor(th, dtype=torch.float64, device=DEV), packed(xs, dt))
         AH = prob.apply_H(0, x, th)
@@ -130,7 +130,7 @@ def test_rminres_nsc_fp64():
     w_prev = None
     tol, scale = 1e-6, 2.5
     for i in range(3):
-        xs, _ = prob.solve_lower(th, gtol=1e-10)
+        xs, _ = prob.solve_lower(th, gtol=1e-8)
         x = xs[0]
         P.set_point(torch.tensor(th, dtype=torch.float64, device=DEV), packed(xs, dt))
         AH = prob.apply_H(0, x, th)
@@ -161,7 +161,7 @@ def test_minres_hypergradient_fp32():
     wl = small_wl(sizes=((56, 56), (40, 72)), N=4, seed=11)
     P, prob, dt = make(wl, "fp32", max_recycle=8, max_basis=60)
     th = r32(wl.theta0)
-    xs = [r32(x) for x in prob.solve_lower(th, gtol=1e-9)[0]]
+    xs = [r32(x) for x in prob.solve_lower(th, gtol=1e-8)[0]]
     P.set_point(torch.tensor(th, dtype=torch.float64, device=DEV), packed(xs, dt))
     w = P.zeros()
     P.hessian_solve(w, recycle=False, tol=1e-6, relative=True, maxit=3000, method="minres", warm_start=False)

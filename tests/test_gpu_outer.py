@@ -32,7 +32,7 @@ def test_nsc_stopping_matches_checker_fp64():
     w_prev = None
     tol, scale = 1e-6, 2.5
     for i in range(3):
-        xs, _ = prob.solve_lower(th, gtol=1e-10)
+        xs, _ = prob.solve_lower(th, gtol=1e-8)
         x = xs[0]
         P.set_point(torch.tensor(th, dtype=torch.float64, device=DEV), packed(xs, dt))
         AH = prob.apply_H(0, x, th)
@@ -93,13 +93,14 @@ def test_autograd_backward_matches_checker_and_fd_fp64():
     L.backward()
     grad = theta.grad.cpu().numpy()
     # checker: the same hypergradient from its own lower solve and dense reference solve
-    xs, _ = prob.solve_lower(wl.theta0, gtol=1e-9)
+    # (5e-9: FP64 Armijo steps stop resolving decreases of Phi just above 1e-9 on this problem)
+    xs, _ = prob.solve_lower(wl.theta0, gtol=5e-9)
     ws = [prob.reference_w(k, xs[k], wl.theta0) for k in range(P.K)]
     ref = prob.hypergradient(wl.theta0, xs, ws)
     assert rel(grad, ref) < 1e-6, rel(grad, ref)
     # central finite differences of L along random directions (lower solves on the GPU, FP64)
     rng = np.random.default_rng(0)
-    h = 1e-4
+    h = 1e-3     # the lower solves' stopping error enters the difference divided by 2h
     for _ in range(3):
         d = rng.standard_normal(P.p)
         d /= np.linalg.norm(d)

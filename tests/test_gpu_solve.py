@@ -16,7 +16,7 @@ from tests.gpu_util import DEV, make, packed, r32, rel, split
 pytestmark = pytest.mark.gpu
 
 
-def lower_points(prob, th, gtol=1e-9):
+def lower_points(prob, th, gtol=1e-8):
     xs, _ = prob.solve_lower(th, gtol=gtol)
     return xs
 
@@ -61,7 +61,7 @@ def test_recycled_sequence_fp64_matches_checker():
     w_prev = None
     s = 6
     for i in range(3):
-        xs = lower_points(prob, th, gtol=1e-10)
+        xs = lower_points(prob, th, gtol=1e-8)
         x = xs[0]
         theta = torch.tensor(th, dtype=torch.float64, device=DEV)
         P.set_point(theta, packed(xs, dt))
