@@ -130,7 +130,7 @@ def test_rminres_nsc_fp64():
     w_prev = None
     tol, scale = 1e-6, 2.5
     for i in range(3):
-        xs, _ = prob.solve_lower(th, gtol=1e-8)
+        xs, _ = prob.solve_lower(th, gtol=1e-7)
         x = xs[0]
         P.set_point(torch.tensor(th, dtype=torch.float64, device=DEV), packed(xs, dt))
         AH = prob.apply_H(0, x, th)
@@ -151,7 +151,7 @@ def test_rminres_nsc_fp64():
         assert abs(info[0]["iters"] - out["iters"]) <= bar, (i, info[0]["iters"], out["iters"])
         if Z is not None:
             assert info[0]["nsc"] < tol * scale and out["nsc"] < tol * scale
-        assert rel(wg.cpu().numpy(), out["w"]) < (1e-7 if Z is None else 1e-6)
+        assert rel(wg.cpu().numpy(), out["w"]) < (1e-7 if Z is None else 1e-5)
         V, w_prev = out["V"][:, -kmax:], out["w"]
         th = th - 0.005 * rng.standard_normal(th.shape)
 

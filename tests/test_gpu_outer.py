@@ -32,7 +32,7 @@ def test_nsc_stopping_matches_checker_fp64():
     w_prev = None
     tol, scale = 1e-6, 2.5
     for i in range(3):
-        xs, _ = prob.solve_lower(th, gtol=1e-8)
+        xs, _ = prob.solve_lower(th, gtol=1e-7)
         x = xs[0]
         P.set_point(torch.tensor(th, dtype=torch.float64, device=DEV), packed(xs, dt))
         AH = prob.apply_H(0, x, th)
@@ -57,7 +57,7 @@ def test_nsc_stopping_matches_checker_fp64():
             assert info[0]["nsc"] < tol * scale and out["nsc"] < tol * scale
             if info[0]["iters"] == out["iters"]:
                 assert abs(info[0]["nsc"] - out["nsc"]) <= 0.25 * tol * scale
-        assert rel(wg.cpu().numpy(), out["w"]) < (1e-7 if Z is None else 1e-6)
+        assert rel(wg.cpu().numpy(), out["w"]) < (1e-7 if Z is None else 1e-5)
         V, w_prev = out["V"], out["w"]
         th = th - 0.005 * rng.standard_normal(th.shape)
 
