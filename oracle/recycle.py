@@ -14,6 +14,10 @@ gsvd_closed_form J~ T^{-1} = V_J diag(mu) V_H^T (eq. (3.4)), X = T^{-1} V_H D_H,
 rgsv             Ritz generalized singular vectors, sides R (W~ X), L (W~ V_H),
                  M (the average), sizes S / L / M (Table 1).
 qr_normalise     H U~ = C R, U = U~ R^{-1}, so that C = H U and C^T C = I (Section 2.2.2).
+refresh          the outer variant (eq. (3.3)): W projected with the current Hessian H^(i).
+refresh_inner    the inner variant (eq. (3.4)): W projected with the previous Hessian H^(i-1)
+                 (the one the basis V was built with); the selected U~ is then paired with
+                 C = H^(i) U (QR-normalised) for the new system.
 """
 from __future__ import annotations
 
@@ -156,3 +160,29 @@ def refresh(U_prev, V_prev, apply_H, apply_J, s, kind="rgsv", which="L", side="R
         raise ValueError(kind)
     U, C = qr_normalise(Wt @ Y, HWt @ Y)
     return U, C, Z, vals
+
+
+def refresh_inner(U_prev, V_prev, apply_H_old, apply_H_new, apply_J, s, kind="ritz", which="S", side="R",
+                  rtol=1e-10):
+    """Inner recycle refresh (Section 3.1, eq. (3.4)): W = [U^(i-1), V^(i-1)], the projected
+    problem built with H^(i-1) (J at the current point for Ritz generalized singular vectors);
+    then C = H^(i) U~ R^{-1} by QR (Section 2.2.2), so the new system's C = H U, C^T C = I.
+    Returns (U, C, Z, values) as refresh()."""
+    W = np.hstack([U_prev, V_prev])
+    Wt = orth_basis(W, rtol)
+    HWt = np.stack([apply_H_old(Wt[:, j]) for j in range(Wt.shape[1])], axis=1)
+    Z = None
+    if kind == "ritz":
+        Y, vals = ritz(Wt, HWt, s, which)
+    elif kind == "hritz":
+        Y, vals = harmonic_ritz(Wt, HWt, s, which)
+    elif kind == "rgsv":
+        JWt = np.stack([apply_J(Wt[:, j]) for j in range(Wt.shape[1])], axis=1)
+        Y, Z, vals = rgsv(Wt, HWt, JWt, s, which, side)
+    else:
+        raise ValueError(kind)
+    Ut = Wt @ Y
+    HUt = np.stack([apply_H_new(Ut[:, j]) for j in range(Ut.shape[1])], axis=1)
+    U, C = qr_normalise(Ut, HUt)
+    return U, C, Z, vals
+

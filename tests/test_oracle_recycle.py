@@ -145,3 +145,37 @@ def test_orth_basis_drops_dependent_columns(rng):
     Wt = rc.orth_basis(W)
     assert Wt.shape == (20, 4)
     np.testing.assert_allclose(Wt.T @ Wt, np.eye(4), atol=1e-12)
+
+
+def test_refresh_inner_reduces_to_outer_when_the_hessian_is_unchanged(rng):
+    """eq. (3.4) with H^(i-1) = H^(i) is eq. (3.3): the same recycle space, C and U."""
+    n, s = 40, 5
+    H = spd(rng, n, 1e3)
+    J = rng.standard_normal((9, n))
+    Up = rng.standard_normal((n, 4))
+    Vp = rc.orth_basis(rng.standard_normal((n, 10)))
+    for kind, which in [("ritz", "S"), ("rgsv", "L"), ("hritz", "L")]:
+        U1, C1, Z1, v1 = rc.refresh(Up, Vp, lambda v: H @ v, lambda v: J @ v, s, kind, which)
+        U2, C2, Z2, v2 = rc.refresh_inner(Up, Vp, lambda v: H @ v, lambda v: H @ v, lambda v: J @ v, s, kind, which)
+        np.testing.assert_allclose(v1, v2, rtol=1e-10)
+        np.testing.assert_allclose(C1, C2, atol=1e-9)
+        np.testing.assert_allclose(U1, U2, atol=1e-9 * np.abs(U1).max())
+
+
+def test_refresh_inner_selects_with_the_old_hessian(rng):
+    """The inner space is the Ritz space of H^(i-1) on W; its C pairs it with H^(i)."""
+    n, s = 40, 5
+    Hold = spd(rng, n, 1e3)
+    E = rng.standard_normal((n, n))
+    Hnew = Hold + 0.05 * (E + E.T)
+    Up = rng.standard_normal((n, 4))
+    Vp = rc.orth_basis(rng.standard_normal((n, 10)))
+    U, C, _, vals = rc.refresh_inner(Up, Vp, lambda v: Hold @ v, lambda v: Hnew @ v, None, s, "ritz", "S")
+    Uo, _, _, valso = rc.refresh(Up, Vp, lambda v: Hold @ v, None, s, "ritz", "S")
+    np.testing.assert_allclose(vals, valso, rtol=1e-10)
+    # same subspace as the outer selection with the old Hessian
+    Q1, _ = np.linalg.qr(U)
+    Q2, _ = np.linalg.qr(Uo)
+    assert np.linalg.svd(Q1.T @ Q2, compute_uv=False).min() > 1 - 1e-10
+    np.testing.assert_allclose(Hnew @ U, C, atol=1e-8)
+    np.testing.assert_allclose(C.T @ C, np.eye(s), atol=1e-10)
