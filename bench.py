@@ -176,9 +176,10 @@ def gpu_arm(args, rank, world, dist):
                 P.set_data(y_d, xs_d)
             P.lower_solve(theta_d, xhat, gtol=LOWER_GTOL, relative=True, max_iters=2000, allow_noconv=True)
             if strat.recycles and state["t"] > 0:
-                P.ritz_update(strat, s_rec)
+                P.ritz_update(strat, s_rec, variant=args.refresh)
             info = P.hessian_solve(w, recycle=strat.recycles, nsc=strat.nsc, tol=rtol, relative=True, maxit=3000,
-                                   store_basis=strat.recycles, warm_start=True,
+                                   store_basis=(("lanczos" if args.refresh == "inner" else True)
+                                                if strat.recycles else False), warm_start=True,
                                    nsc_scale=None if hg_prev is None else [hg_prev] * K, allow_noconv=True,
                                    method=args.method, graph=args.graph)
             mean, per = P.hypergrad(w, per_pair=True)
@@ -323,6 +324,9 @@ def main():
     ap.add_argument("--workload", default="batch64", choices=["batch64", "inpaint"],
                     help="batch64: the 64-pair deconvolution batch (the metric's workload); inpaint: 1024 "
                          "inpainting pairs shaped like the paper's Section 5.1 experiment")
+    ap.add_argument("--refresh", default="outer", choices=["outer", "inner"],
+                    help="recycle refresh: outer (eq. (3.3), current Hessian) or inner (eq. (3.4), the last "
+                         "solve's Hessian through its Lanczos record; CG only)")
     ap.add_argument("--method", default="cg", choices=["cg", "minres"],
                     help="Krylov method of the Hessian solves: (recycled) CG or (recycled) MINRES")
     ap.add_argument("--max-basis", type=int, default=MAX_BASIS,
@@ -405,7 +409,7 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": out["wdesc"] or (f"batch64_foe_n16f5: {K} pairs, sides 128-512, {n_pix} px, "
                                                 f"16 5x5 filters, 9x9 blur, p={wl.n_params}"),
-                   "strategy": out["strategy"].acronym(), "krylov": args.method, "recycle_dim": out["s_rec"], "max_basis": args.max_basis,
+                   "strategy": out["strategy"].acronym(), "refresh": args.refresh, "krylov": args.method, "recycle_dim": out["s_rec"], "max_basis": args.max_basis,
                    "stop": f"residual rtol {INPAINT_RTOL if args.workload == 'inpaint' else RTOL}", "lower_gtol_rel": LOWER_GTOL, "outer": "Adam lr 1e-2",
                    "l2": "inputs larger than L2 (batch working set > 1 GB), no flush"},
         "hg_rel_err_max": rec.get("hg_err_max"), "hg_rel_err_mean_grad": rec.get("hg_err_mean_grad"),

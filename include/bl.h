@@ -103,6 +103,14 @@ typedef struct {
    build (normalised CG residuals / Lanczos vectors) for bl_ritz_update. */
 typedef enum { BL_SOLVE_CG = 0, BL_SOLVE_RCG = 1, BL_SOLVE_MINRES = 2, BL_SOLVE_RMINRES = 3 } bl_solve_method;
 typedef enum { BL_STOP_RESID = 0, BL_STOP_NSC = 1 } bl_stop_rule;
+/* Basis kept by bl_hessian_solve for the next refresh:
+ *   BL_STORE_NONE
+ *   BL_STORE_RECENT   the most recent max_basis basis vectors (CG: normalised residuals; MINRES:
+ *                     Lanczos vectors), for the outer refresh (eq. (3.3));
+ *   BL_STORE_LANCZOS  (CG only) the first max_basis normalised residuals with the CG coefficients
+ *                     alpha_j, rho_j and C^T H p_j, from which the refresh rebuilds H V through the
+ *                     Lanczos relation of the projected operator: the inner refresh (eq. (3.4)). */
+typedef enum { BL_STORE_NONE = 0, BL_STORE_RECENT = 1, BL_STORE_LANCZOS = 2 } bl_store_mode;
 
 typedef struct {
   int32_t method;        /* BL_SOLVE_CG / BL_SOLVE_MINRES ignore the recycle space; BL_SOLVE_RCG /
@@ -114,8 +122,7 @@ typedef struct {
   int32_t relative;      /* RESID: scale = ||g_k|| if non-zero, else 1.
                             NSC:   scale = nsc_scale[k] from bl_hessian_solve, else 1. */
   int32_t maxit;
-  int32_t store_basis;   /* keep the basis (CG: normalised residuals; MINRES: Lanczos vectors) as V
-                            for the next bl_ritz_update */
+  int32_t store_basis;   /* bl_store_mode: keep the basis for the next bl_ritz_update */
   int32_t warm_start;    /* non-zero: w (in) is the initial guess; zero: start from 0 */
   int32_t graph;         /* non-zero: run the iteration loop as one CUDA-graph launch (a WHILE node whose
                             condition is set on the device), without host round trips; the stream path
@@ -126,12 +133,19 @@ typedef enum { BL_RECYCLE_RITZ = 0, BL_RECYCLE_HRITZ = 1, BL_RECYCLE_RGSV = 2 } 
 typedef enum { BL_SIZE_SMALL = 0, BL_SIZE_LARGE = 1, BL_SIZE_MIXED = 2 } bl_recycle_size;
 typedef enum { BL_SIDE_RIGHT = 0, BL_SIDE_LEFT = 1, BL_SIDE_MIXED = 2 } bl_recycle_side;
 
+/* Which Hessian projects W = [U, V] (Section 3.1): the current one, W^T H^(i) W (eq. (3.3), t Hessian
+ * actions), or the one V was built with, W^T H^(i-1) W (eq. (3.4)), rebuilt from the stored CG
+ * coefficients without Hessian actions; the selected U is then paired with C = H^(i) U (s actions). */
+typedef enum { BL_REFRESH_OUTER = 0, BL_REFRESH_INNER = 1 } bl_refresh_variant;
+
 /* Table 1 grammar: Ritz-S = {RITZ, SMALL}, RGen-L(R) = {RGSV, LARGE, RIGHT}. */
 typedef struct {
   int32_t kind;          /* bl_recycle_kind */
   int32_t size;          /* bl_recycle_size */
   int32_t side;          /* bl_recycle_side (RGSV only) */
   int32_t s;             /* recycle dimension, 1..max_recycle; RGSV also needs s <= p */
+  int32_t variant;       /* bl_refresh_variant; INNER needs the last solve's BL_STORE_LANCZOS basis
+                            (BL_ESTATE otherwise) */
 } bl_recycle_opts;
 
 typedef struct {

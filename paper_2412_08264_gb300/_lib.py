@@ -23,6 +23,8 @@ BL_STOP_RESID, BL_STOP_NSC = 0, 1
 BL_RECYCLE = {"ritz": 0, "hritz": 1, "rgsv": 2}
 BL_SIZE = {"S": 0, "L": 1, "M": 2}
 BL_SIDE = {"R": 0, "L": 1, "M": 2}
+BL_REFRESH = {"outer": 0, "inner": 1}
+BL_STORE_NONE, BL_STORE_RECENT, BL_STORE_LANCZOS = 0, 1, 2
 KERNEL_CLASSES = ["hvp", "hvp_multi", "grad", "jw", "krylov", "lbfgs", "gram", "gemm", "dense", "other"]
 
 
@@ -49,7 +51,8 @@ class KrylovOpts(C.Structure):
 
 
 class RecycleOpts(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("size", C.c_int32), ("side", C.c_int32), ("s", C.c_int32)]
+    _fields_ = [("kind", C.c_int32), ("size", C.c_int32), ("side", C.c_int32), ("s", C.c_int32),
+                ("variant", C.c_int32)]
 
 
 class SolveInfo(C.Structure):

@@ -144,12 +144,16 @@ class Problem:
         L.check(self.lib.bl_hvp(self.h, pa, n, _ptr(v), _ptr(out)), "bl_hvp")
         return out
 
-    def ritz_update(self, strategy, s: int, pairs=None):
+    def ritz_update(self, strategy, s: int, pairs=None, variant: str = "outer"):
+        """variant "outer": project W with the current Hessian (eq. (3.3)); "inner": with the Hessian
+        of the last solve, rebuilt from its Lanczos record (eq. (3.4); that solve must have used
+        store_basis="lanczos")."""
         st = parse(strategy) if isinstance(strategy, str) else strategy
         if not st.recycles:
             return
         pa, n, _ = self._pairs(pairs)
-        o = L.RecycleOpts(L.BL_RECYCLE[st.kind], L.BL_SIZE[st.size], L.BL_SIDE[st.side], int(s))
+        o = L.RecycleOpts(L.BL_RECYCLE[st.kind], L.BL_SIZE[st.size], L.BL_SIDE[st.side], int(s),
+                          L.BL_REFRESH[variant])
         L.check(self.lib.bl_ritz_update(self.h, pa, n, C.byref(o)), "bl_ritz_update")
 
     def hessian_solve(self, w: torch.Tensor, g: Optional[torch.Tensor] = None, pairs=None, recycle: bool = True,
@@ -157,7 +161,9 @@ class Problem:
                       store_basis: bool = True, warm_start: bool = True, nsc_scale=None, allow_noconv=False,
                       graph: bool = True, method: str = "cg"):
         """method "cg": (recycled) CG, SPD Hessians; "minres": (recycled) MINRES (Algorithm 3),
-        symmetric indefinite Hessians."""
+        symmetric indefinite Hessians.  store_basis: False, True (the most recent basis vectors, for
+        the outer refresh) or "lanczos" (CG: the first basis vectors with the CG coefficients, for
+        the inner refresh)."""
         pa, n, idx = self._pairs(pairs)
         self._check_images(w, idx)
         if g is not None:
@@ -168,8 +174,10 @@ class Problem:
             meth = L.BL_SOLVE_RCG if recycle else L.BL_SOLVE_CG
         else:
             meth = L.BL_SOLVE_RMINRES if recycle else L.BL_SOLVE_MINRES
+        store = (L.BL_STORE_LANCZOS if store_basis == "lanczos"
+                 else (L.BL_STORE_RECENT if store_basis else L.BL_STORE_NONE))
         o = L.KrylovOpts(meth, L.BL_STOP_NSC if nsc else L.BL_STOP_RESID,
-                         float(tol), 1 if relative else 0, int(maxit), 1 if store_basis else 0,
+                         float(tol), 1 if relative else 0, int(maxit), store,
                          1 if warm_start else 0, 1 if graph else 0)
         sc = None
         if nsc_scale is not None:

@@ -157,6 +157,10 @@ struct bl_problem {
   void *mv_prev = nullptr, *my1 = nullptr, *my2 = nullptr;
   double* mrs = nullptr;
   unsigned char* d_opmask = nullptr;   // inpainting masks of all pairs (n_tot bytes), if any pair has one
+  // Lanczos-relation record of the last CG solve (BL_STORE_LANCZOS): per pair and step j < KMAX,
+  // alpha_j, rho_j = ||r_j||^2 and C^T H p_j; lz_k[k] = 1 when pair k's stored basis is such a record
+  double *lz_alpha = nullptr, *lz_rho = nullptr, *lz_c = nullptr;
+  std::vector<int> lz_k;
   void *U = nullptr, *C = nullptr, *Z = nullptr, *V = nullptr;
   void *W = nullptr, *Wt = nullptr, *HWt = nullptr;
   bl::SolveState* st = nullptr;

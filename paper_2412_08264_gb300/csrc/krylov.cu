@@ -47,6 +47,9 @@ struct KrylovArgs {
   const double* tpart;
   int n_tiles, n_chunks;
   double *b1, *b2, *h1, *h2;   // MINRES: beta~_{k-1}, beta~_{k-2}, Z^T Hvt_{k-1}, Z^T Hvt_{k-2} (K x SMAX)
+  // CG Lanczos record (BL_STORE_LANCZOS): alpha_j, rho_j (K x KMAX), C^T H p_j (K x KMAX x SMAX)
+  int lanczos;
+  double *lz_alpha, *lz_rho, *lz_c;
 };
 
 // Per-chunk partial sums of up to 64 components, one warp total each, written to part[chunk][off + m].
@@ -213,6 +216,7 @@ __global__ void k_scalar_init2(KrylovArgs a, const int* mask, int stop_nsc, doub
     }
     S.tol = tol * scale;
     S.est = est;
+    if (a.lanczos && a.KMAX > 0) a.lz_rho[(size_t)k * a.KMAX] = S.rho;
     S.active = (est >= S.tol && maxit > 0 && S.rho > 0.0) ? 1 : 0;
     if (!isfinite(S.rho)) {
       S.active = 0;
@@ -295,9 +299,13 @@ __global__ void k_scalar1(KrylovArgs a, int use_tiles) {
   }
   __syncthreads();
   const double al = alpha_s;
+  const int it = a.st[k].iters;
+  const bool rec = a.lanczos && it < a.KMAX;
+  if (rec && threadIdx.x == 0) a.lz_alpha[(size_t)k * a.KMAX + it] = al;
   for (int m = threadIdx.x; m < s; m += blockDim.x) {
     a.c[k * a.SMAX + m] = sh[1 + m];
     a.zc[k * a.SMAX + m] -= al * sh[1 + m];
+    if (rec) a.lz_c[((size_t)k * a.KMAX + it) * a.SMAX + m] = sh[1 + m];
   }
 }
 
@@ -320,14 +328,16 @@ __global__ void k_update(KrylovArgs a, T* w, T* r, const T* p, const T* q, const
   __syncthreads();
   const T* Cb = C + pr.off * a.SMAX;
   const T* Zb = Z + pr.off * a.SMAX;
-  T* Vc = store ? V + pr.off * a.KMAX + (long long)(S.iters % a.KMAX) * pr.n : nullptr;
+  // store 1: ring of the most recent KMAX residuals; store 2: the first KMAX (Lanczos record)
+  const bool st_now = store == 1 || (store == 2 && S.iters < a.KMAX);
+  T* Vc = st_now ? V + pr.off * a.KMAX + (long long)(S.iters % a.KMAX) * pr.n : nullptr;
   const T inv_nr = (T)(1.0 / sqrt(S.rho));
   const T al = (T)S.alpha;
   Accum<T> rho;
   for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
     const long long li = ch.start + t, gi = pr.off + li;
     const T ro = r[gi];
-    if (store) Vc[li] = ro * inv_nr;
+    if (Vc) Vc[li] = ro * inv_nr;
     w[gi] = fma(al, p[gi], w[gi]);
     T ccv = 0;
     for (int j = 0; j < s; ++j) ccv = fma(cs[j], Cb[(long long)j * pr.n + li], ccv);
@@ -380,6 +390,7 @@ __global__ void k_scalar2(KrylovArgs a, int stop_nsc, int* flag) {
     S.beta = rho_new / S.rho;
     S.rho = rho_new;
     S.iters += 1;
+    if (a.lanczos && S.iters < a.KMAX) a.lz_rho[(size_t)k * a.KMAX + S.iters] = rho_new;
     if (nz > 0) {
       double z2 = 0.0;
       for (int m = 0; m < nz; ++m) {
@@ -415,6 +426,20 @@ __global__ void k_pupdate(KrylovArgs a, const T* r, T* p) {
     const long long gi = pr.off + ch.start + t;
     p[gi] = fma(be, p[gi], r[gi]);
   }
+}
+
+// Lanczos record: the residual after the last step, normalised, as basis vector `iters` (zero if the
+// residual vanished), so that H V_m = V_{m+1} T_m + C B_m can be formed for m = min(iters, KMAX - 1)
+template <typename T>
+__global__ void k_store_last(KrylovArgs a, const T* r, T* V, const int* mask) {
+  const ChunkDev ch = a.chunks[blockIdx.x];
+  if (!mask[ch.pair]) return;
+  const SolveState S = a.st[ch.pair];
+  if (S.iters >= a.KMAX) return;
+  const PairDev pr = a.pairs[ch.pair];
+  T* Vc = V + pr.off * a.KMAX + (long long)S.iters * pr.n;
+  const T sc = S.rho > 0.0 ? (T)(1.0 / sqrt(S.rho)) : T(0);
+  for (int t = threadIdx.x; t < ch.len; t += blockDim.x) Vc[ch.start + t] = r[pr.off + ch.start + t] * sc;
 }
 
 // w += U z
@@ -772,6 +797,10 @@ static bl_status solve_impl(bl_problem* P, const int* mask_host, const bl_krylov
   a.tpart = P->tpart;
   a.n_tiles = P->n_tiles;
   a.n_chunks = P->n_chunks;
+  a.lanczos = (o->store_basis == BL_STORE_LANCZOS && P->KMAX > 0) ? 1 : 0;
+  a.lz_alpha = P->lz_alpha;
+  a.lz_rho = P->lz_rho;
+  a.lz_c = P->lz_c;
   if (minres) {
     const size_t ks = (size_t)K * std::max(P->SMAX, 1);
     a.b1 = P->mrs;
@@ -819,7 +848,7 @@ static bl_status solve_impl(bl_problem* P, const int* mask_host, const bl_krylov
   // ---- iterations ----
   // the per-pair `active` flags gate every kernel; the loop ends when no pair is active
   int* d_itmask = P->d_active + K; // per-pair active copy for the stencil mask
-  const int store = (o->store_basis && P->KMAX > 0) ? 1 : 0;
+  const int store = P->KMAX > 0 ? (o->store_basis == BL_STORE_LANCZOS ? 2 : (o->store_basis ? 1 : 0)) : 0;
   const int nsc = o->stop == BL_STOP_NSC ? 1 : 0;
   auto iteration = [&]() -> bl_status {
     {
@@ -913,6 +942,10 @@ static bl_status solve_impl(bl_problem* P, const int* mask_host, const bl_krylov
   }
   {
     ProfScope ps(P, BL_KC_KRYLOV);
+    if (a.lanczos) {
+      k_store_last<T><<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a, r, (T*)P->V, mask);
+      BL_LAUNCH_CHECK(P);
+    }
     k_finalize<T><<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a, w, U, mask);
     BL_LAUNCH_CHECK(P);
   }
@@ -938,8 +971,10 @@ static bl_status solve_impl(bl_problem* P, const int* mask_host, const bl_krylov
     info[k].nsc_est = std::sqrt(z2);
     info[k].rhs_norm = std::sqrt(std::max(S.gnorm2, 0.0));
     if (o->store_basis && P->KMAX > 0) {
-      P->kb_k[k] = std::min(S.iters, P->KMAX);
+      // Lanczos record: v_0 .. v_{m-1} form the basis, v_m closes the relation
+      P->kb_k[k] = a.lanczos ? std::min(S.iters, P->KMAX - 1) : std::min(S.iters, P->KMAX);
       P->head_k[k] = S.iters;
+      P->lz_k[k] = a.lanczos;
     }
   }
   return BL_OK;

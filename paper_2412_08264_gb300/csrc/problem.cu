@@ -180,7 +180,7 @@ void bl_problem_destroy(bl_problem* P) {
                   P->d_active, P->d_cols, P->d_flag, P->dG, P->dT, P->dJ, P->dY, P->dY2, P->dY3, P->d_tk,
                   P->lx, P->lg, P->ld, P->lxt, P->lgt, P->lq, P->S, P->Yh, P->lsy, P->lyy, P->lcs, P->lcy,
                   P->lst, P->tpart, P->cpart, P->vals,
-                  P->d_pix, P->d_zero, P->d_loop, P->mv_prev, P->my1, P->my2, P->mrs, P->d_opmask};
+                  P->d_pix, P->d_zero, P->d_loop, P->mv_prev, P->my1, P->my2, P->mrs, P->d_opmask, P->lz_alpha, P->lz_rho, P->lz_c};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (P->h_flag) cudaFreeHost(P->h_flag);
@@ -292,6 +292,7 @@ bl_status bl_problem_create(const bl_pair_desc* pairs, int32_t K, const bl_reg_d
   P->kb_k.assign(K, 0);
   P->hz_k.assign(K, 0);
   P->head_k.assign(K, 0);
+  P->lz_k.assign(K, 0);
 
   bl_status st = BL_OK;
 #define BL_ALLOC(expr)              \
@@ -342,6 +343,12 @@ bl_status bl_problem_create(const bl_pair_desc* pairs, int32_t K, const bl_reg_d
   for (double** b : {&P->c, &P->zc, &P->e, &P->ztr})
     BL_ALLOC(dalloc((void**)b, (size_t)K * P->SMAX * sizeof(double)));
   BL_ALLOC(dalloc((void**)&P->ztc, (size_t)K * P->SMAX * P->SMAX * sizeof(double)));
+  {
+    const size_t kk = (size_t)K * std::max(1, P->KMAX);
+    BL_ALLOC(dalloc((void**)&P->lz_alpha, kk * sizeof(double)));
+    BL_ALLOC(dalloc((void**)&P->lz_rho, kk * sizeof(double)));
+    BL_ALLOC(dalloc((void**)&P->lz_c, kk * P->SMAX * sizeof(double)));
+  }
   BL_ALLOC(dalloc((void**)&P->d_s, K * sizeof(int)));
   BL_ALLOC(dalloc((void**)&P->d_hasz, K * sizeof(int)));
   BL_ALLOC(dalloc((void**)&P->d_active, 3 * K * sizeof(int)));
@@ -504,6 +511,7 @@ bl_status bl_ritz_update(bl_problem* P, const int32_t* pairs, int32_t npairs, co
     return fail(BL_EINVAL, "unknown recycle option");
   if (o->s < 1 || o->s > P->reg.max_recycle) return fail(BL_EINVAL, "s must be in 1..max_recycle");
   if (o->kind == BL_RECYCLE_RGSV && o->s > P->p) return fail(BL_EINVAL, "RGSV needs s <= p");
+  if (o->variant != BL_REFRESH_OUTER && o->variant != BL_REFRESH_INNER) return fail(BL_EINVAL, "unknown refresh variant");
   if ((st = set_active_pairs(P, pairs, npairs)) != BL_OK) return st;
   return run_ritz_update(P, host_mask(P, pairs, npairs), o);
 }
@@ -517,6 +525,10 @@ bl_status bl_hessian_solve(bl_problem* P, const int32_t* pairs, int32_t npairs, 
   if (o->method < BL_SOLVE_CG || o->method > BL_SOLVE_RMINRES) return fail(BL_EINVAL, "unknown solve method");
   if (o->stop != BL_STOP_RESID && o->stop != BL_STOP_NSC) return fail(BL_EINVAL, "unknown stop rule");
   if (o->maxit < 0 || !(o->tol >= 0.0)) return fail(BL_EINVAL, "invalid Krylov options");
+  if (o->store_basis < BL_STORE_NONE || o->store_basis > BL_STORE_LANCZOS)
+    return fail(BL_EINVAL, "unknown store mode");
+  if (o->store_basis == BL_STORE_LANCZOS && (o->method == BL_SOLVE_MINRES || o->method == BL_SOLVE_RMINRES))
+    return fail(BL_EINVAL, "BL_STORE_LANCZOS records CG steps; MINRES keeps BL_STORE_RECENT");
   if ((st = set_active_pairs(P, pairs, npairs)) != BL_OK) return st;
   if (o->warm_start && (st = gather_packed(P, pairs, npairs, w, P->w)) != BL_OK) return st;
   if (g) {

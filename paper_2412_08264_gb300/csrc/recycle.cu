@@ -202,7 +202,7 @@ __global__ void k_dense_orth(DenseArgs a, const int* tcols) {
   if (!a.mask[k]) return;
   const int t = tcols[k], TM = a.TM;
   double* As = reinterpret_cast<double*>(smem_raw);   // t x t scaled Gram, updated in place
-  double* Rs = As + TM * TM;                          // t' x t' factor (row j: R[j][*], kept order)
+  double* Rs = As + TM * TM;                          // factor rows; row j indexed by original column
   double* dsc = Rs + TM * TM;
   double* dres = dsc + TM;                            // remaining pivots
   int* piv = reinterpret_cast<int*>(dres + TM);
@@ -240,17 +240,18 @@ __global__ void k_dense_orth(DenseArgs a, const int* tcols) {
     if (s_stop) break;
     const int pj = piv[j];
     const double rjj = sqrt(dres[pj]);
-    // row j of R over the remaining columns (kept order), from the updated Schur complement
+    // row j of R over the remaining columns, from the updated Schur complement.  Entries are kept
+    // under the original column index: later pivot swaps reorder positions, not columns.
     for (int i = j + threadIdx.x; i < t; i += blockDim.x) {
       const int pi = piv[i];
-      Rs[j * TM + i] = (i == j) ? rjj : As[pj * t + pi] / rjj;
+      Rs[j * TM + pi] = (i == j) ? rjj : As[pj * t + pi] / rjj;
     }
     __syncthreads();
-    // trailing update A[pi][pl] -= R[j][i] R[j][l], i, l > j; remaining pivots
+    // trailing update A[pi][pl] -= R[j][pi] R[j][pl] over the columns still to be pivoted
     const int m = t - j - 1;
     for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
-      const int ii = j + 1 + idx / m, ll = j + 1 + idx % m;
-      As[piv[ii] * t + piv[ll]] -= Rs[j * TM + ii] * Rs[j * TM + ll];
+      const int pi = piv[j + 1 + idx / m], pl = piv[j + 1 + idx % m];
+      As[pi * t + pl] -= Rs[j * TM + pi] * Rs[j * TM + pl];
     }
     __syncthreads();
     for (int i = j + 1 + threadIdx.x; i < t; i += blockDim.x) dres[piv[i]] = As[piv[i] * t + piv[i]];
@@ -262,13 +263,14 @@ __global__ void k_dense_orth(DenseArgs a, const int* tcols) {
   double* Y = a.Y + (size_t)k * TM * TM;   // t x t'
   for (int idx = threadIdx.x; idx < t * tk; idx += blockDim.x) Y[(idx / tk) * TM + idx % tk] = 0.0;
   __syncthreads();
+  // in pivoted order R_pos[i][l] = Rs[i][piv[l]] (upper triangular over the kept columns)
   for (int c = threadIdx.x; c < tk; c += blockDim.x) {
     double x[kMaxTM];
     for (int i = c + 1; i < tk; ++i) x[i] = 0.0;
     for (int i = c; i >= 0; --i) {
       double v = (i == c) ? 1.0 : 0.0;
-      for (int l = i + 1; l <= c; ++l) v -= Rs[i * TM + l] * x[l];
-      x[i] = v / Rs[i * TM + i];
+      for (int l = i + 1; l <= c; ++l) v -= Rs[i * TM + piv[l]] * x[l];
+      x[i] = v / Rs[i * TM + piv[i]];
     }
     for (int i = 0; i <= c; ++i) Y[piv[i] * TM + c] = dsc[piv[i]] * x[i];
   }
@@ -451,6 +453,45 @@ __global__ void k_copy_ztc(const int* mask, const int* scols, const double* G, i
   }
 }
 
+// Inner refresh: H^(i-1) [U, V_m] from the last CG solve's record (no Hessian actions).  With
+// C = H U, P H p_j = (r_j - r_{j+1}) / alpha_j and p_j = r_j + beta_{j-1} p_{j-1}:
+//   H V_m = V_{m+1} T_m + C B_m,  T_m (m+1 x m) tridiagonal:
+//     T[j][j] = 1/alpha_j + beta_{j-1}/alpha_{j-1},  T[j+1][j] = -nu_{j+1} / (nu_j alpha_j),
+//     T[j-1][j] = -nu_j / (nu_{j-1} alpha_{j-1});   B[:, j] = (C^T H p_j - beta_{j-1} C^T H p_{j-1}) / nu_j,
+//   nu_j = ||r_j|| = sqrt(rho_j), beta_{j-1} = rho_j / rho_{j-1}.
+// Writes M (s + m + 1 x s + m, ld TM) with H [U, V_m] = [C, V_{m+1}] M.
+__global__ void k_lanczos_rel(const int* mask, const int* s_old, const int* tcols, const double* lz_alpha,
+                              const double* lz_rho, const double* lz_c, int KMAX, int SMAX, int TM, double* M) {
+  const int k = blockIdx.x;
+  if (!mask[k]) return;
+  const int s = s_old[k], t = tcols[k];
+  double* Mk = M + (size_t)k * TM * TM;
+  const double* al = lz_alpha + (size_t)k * KMAX;
+  const double* rh = lz_rho + (size_t)k * KMAX;
+  const double* cc = lz_c + (size_t)k * KMAX * SMAX;
+  for (int idx = threadIdx.x; idx < (t + 1) * t; idx += blockDim.x) {
+    const int i = idx / t, j = idx - (idx / t) * t;
+    double v = 0.0;
+    if (j < s) {
+      v = (i == j) ? 1.0 : 0.0;
+    } else {
+      const int jj = j - s;
+      const double bprev = jj > 0 ? rh[jj] / rh[jj - 1] : 0.0;
+      if (i < s) {
+        double b = cc[(size_t)jj * SMAX + i];
+        if (jj > 0) b -= bprev * cc[(size_t)(jj - 1) * SMAX + i];
+        v = b / sqrt(rh[jj]);
+      } else {
+        const int r = i - s;
+        if (r == jj) v = 1.0 / al[jj] + (jj > 0 ? bprev / al[jj - 1] : 0.0);
+        else if (r == jj + 1) v = -sqrt(rh[jj + 1]) / (sqrt(rh[jj]) * al[jj]);
+        else if (r == jj - 1) v = -sqrt(rh[jj]) / (sqrt(rh[jj - 1]) * al[jj - 1]);
+      }
+    }
+    Mk[i * TM + j] = v;
+  }
+}
+
 template <typename T>
 static bl_status refresh_impl(bl_problem* P, const std::vector<int>& mask_host, const bl_recycle_opts* o) {
   const int K = P->K, TM = P->TM;
@@ -465,6 +506,11 @@ static bl_status refresh_impl(bl_problem* P, const std::vector<int>& mask_host, 
     any = true;
   }
   if (!any) return BL_OK;
+  const bool inner = o->variant == BL_REFRESH_INNER;
+  if (inner)
+    for (int k = 0; k < K; ++k)
+      if (msk[k] && !P->lz_k[k])
+        return fail(BL_ESTATE, "inner refresh needs the last solve's Lanczos record (BL_STORE_LANCZOS)");
   int* d_mask = P->d_active + 2 * K;      // refresh mask
   int* d_t = P->d_cols;                   // t per pair
   int* d_tk = P->d_tk;                    // t' per pair
@@ -486,6 +532,31 @@ static bl_status refresh_impl(bl_problem* P, const std::vector<int>& mask_host, 
   int tmax = 0;
   for (int k = 0; k < K; ++k) tmax = std::max(tmax, tcols[k]);
   const int smax = std::min(o->s, P->SMAX);
+  if (inner) {
+    // H^(i-1) W = [C, V_{m+1}] M from the record: X = [C, V_0 .. V_m] staged in Wt
+    std::vector<int> xc(K, 0);
+    for (int k = 0; k < K; ++k) {
+      if (!msk[k]) continue;
+      const auto& ph = P->ph[k];
+      char* Xk = (char*)P->Wt + ph.off * TM * P->esz;
+      xc[k] = tcols[k] + 1;
+      if (P->s_k[k])
+        BL_CUDA_TRY(cudaMemcpyAsync(Xk, (const char*)P->C + ph.off * P->SMAX * P->esz,
+                                    (size_t)P->s_k[k] * ph.n * P->esz, cudaMemcpyDeviceToDevice, P->stream));
+      BL_CUDA_TRY(cudaMemcpyAsync(Xk + (size_t)P->s_k[k] * ph.n * P->esz, (const char*)P->V + ph.off * P->KMAX * P->esz,
+                                  (size_t)(P->kb_k[k] + 1) * ph.n * P->esz, cudaMemcpyDeviceToDevice, P->stream));
+    }
+    BL_CUDA_TRY(cudaMemcpyAsync(d_tk, xc.data(), K * sizeof(int), cudaMemcpyHostToDevice, P->stream));
+    {
+      ProfScope ps(P, BL_KC_DENSE);
+      k_lanczos_rel<<<K, 256, 0, P->stream>>>(d_mask, P->d_s, d_t, P->lz_alpha, P->lz_rho, P->lz_c, P->KMAX, P->SMAX,
+                                              TM, P->dY2);
+      BL_LAUNCH_CHECK(P);
+    }
+    bl_status sx = ts_gemm(P, P->Wt, TM, d_tk, tmax + 1, P->dY2, P->HWt, TM, d_t, tmax, nullptr, nullptr, 0, nullptr,
+                           0, d_mask);
+    if (sx != BL_OK) return sx;
+  }
   DenseArgs da{};
   da.TM = TM;
   da.p = P->p;
@@ -521,10 +592,16 @@ static bl_status refresh_impl(bl_problem* P, const std::vector<int>& mask_host, 
   }
   st = ts_gemm(P, P->W, TM, d_t, tmax, P->dY, P->Wt, TM, d_tk, tmax, nullptr, nullptr, 0, nullptr, 0, d_mask);
   if (st != BL_OK) return st;
-  // 2. H W~
-  BL_CUDA_TRY(cudaMemcpyAsync(P->d_cols, d_tk, K * sizeof(int), cudaMemcpyDeviceToDevice, P->stream));
-  st = launch_hvp(P, P->Wt, P->HWt, TM, tmax, d_mask, nullptr, nullptr);
-  if (st != BL_OK) return st;
+  // 2. H W~: Hessian actions at the current point (outer), or H^(i-1) W B1 from the record (inner)
+  if (inner) {
+    st = ts_gemm(P, P->HWt, TM, d_t, tmax, P->dY, P->HWt, TM, d_tk, tmax, nullptr, nullptr, 0, nullptr, 0, d_mask);
+    if (st != BL_OK) return st;
+    BL_CUDA_TRY(cudaMemcpyAsync(P->d_cols, d_tk, K * sizeof(int), cudaMemcpyDeviceToDevice, P->stream));
+  } else {
+    BL_CUDA_TRY(cudaMemcpyAsync(P->d_cols, d_tk, K * sizeof(int), cudaMemcpyDeviceToDevice, P->stream));
+    st = launch_hvp(P, P->Wt, P->HWt, TM, tmax, d_mask, nullptr, nullptr);
+    if (st != BL_OK) return st;
+  }
   // 3. projected matrices
   st = ts_gram(P, P->Wt, TM, d_tk, tmax, P->HWt, TM, d_tk, tmax, d_mask, P->dT);
   if (st != BL_OK) return st;
@@ -547,7 +624,13 @@ static bl_status refresh_impl(bl_problem* P, const std::vector<int>& mask_host, 
   st = ts_gemm(P, P->Wt, TM, d_tk, tmax, P->dY, P->U, P->SMAX, d_sn, smax, rgsv ? P->dY2 : nullptr,
                rgsv ? P->Z : nullptr, P->SMAX, d_sn, smax, d_mask);
   if (st != BL_OK) return st;
-  st = ts_gemm(P, P->HWt, TM, d_tk, tmax, P->dY, P->C, P->SMAX, d_sn, smax, nullptr, nullptr, 0, nullptr, 0, d_mask);
+  if (inner) {
+    // C~ = H^(i) U~: the new system's operator (s Hessian actions)
+    BL_CUDA_TRY(cudaMemcpyAsync(P->d_cols, d_sn, K * sizeof(int), cudaMemcpyDeviceToDevice, P->stream));
+    st = launch_hvp(P, P->U, P->C, P->SMAX, smax, d_mask, nullptr, nullptr);
+  } else {
+    st = ts_gemm(P, P->HWt, TM, d_tk, tmax, P->dY, P->C, P->SMAX, d_sn, smax, nullptr, nullptr, 0, nullptr, 0, d_mask);
+  }
   if (st != BL_OK) return st;
   // CholeskyQR2 of C~, applied to U~ as well
   for (int rep = 0; rep < 2; ++rep) {

@@ -35,9 +35,11 @@ class StepInfo:
 class Engine:
     def __init__(self, problem: api.Problem, strategy="RGen-L(R)", s: int = 16, rtol: float = 1e-4,
                  lower_gtol: float = 1e-5, lower_max_iters: int = 5000, maxit: int = 5000,
-                 nsc_tol: Optional[float] = None, lower_relative: bool = True, method: str = "cg"):
+                 nsc_tol: Optional[float] = None, lower_relative: bool = True, method: str = "cg",
+                 refresh: str = "outer"):
         self.P = problem
         self.method = method            # "cg" (SPD Hessians) or "minres" (Algorithm 3, indefinite)
+        self.refresh = refresh          # "outer" (eq. (3.3)) or "inner" (eq. (3.4), CG only)
         self.strategy: Strategy = parse(strategy) if isinstance(strategy, str) else strategy
         self.s = s
         self.rtol = rtol
@@ -62,12 +64,15 @@ class Engine:
         """Refresh + recycled solve + J w at the point set by the last lower solve / set_point."""
         st = self.strategy
         if st.recycles and self.n_systems > 0:
-            self.P.ritz_update(st, self.s)
+            self.P.ritz_update(st, self.s, variant=self.refresh)
         nsc = st.nsc and self.nsc_tol is not None
         tol = self.nsc_tol if nsc else self.rtol
         scale = None if (not nsc or self.hg_prev is None) else [self.hg_prev] * self.P.K
         info = self.P.hessian_solve(self.w, g=g, recycle=st.recycles, nsc=nsc, tol=tol, relative=True,
-                                    maxit=self.maxit, store_basis=st.recycles, warm_start=True, nsc_scale=scale,
+                                    maxit=self.maxit,
+                                    store_basis=(("lanczos" if self.refresh == "inner" else True) if st.recycles
+                                                 else False),
+                                    warm_start=True, nsc_scale=scale,
                                     allow_noconv=True, method=self.method)
         self.n_systems += 1
         mean, per, loss = self.P.hypergrad(self.w, per_pair=True, loss=True)
