@@ -105,7 +105,8 @@ def test_inner_refresh_needs_a_lanczos_record():
     wl = synth.uneven_foe([(30, 31)], n_filters=2, f=3, blur_radius=1, seed=3)
     P, prob, dt = make(wl, "fp32", max_recycle=4, max_basis=20)
     th = r32(wl.theta0)
-    P.set_point(torch.tensor(th, dtype=torch.float64, device=DEV), packed([r32(x) for x in wl.x_star], dt))
+    xs = [r32(x + 0.05 * np.random.default_rng(1).standard_normal(x.shape)) for x in wl.x_star]
+    P.set_point(torch.tensor(th, dtype=torch.float64, device=DEV), packed(xs, dt))
     w = P.zeros()
     P.hessian_solve(w, recycle=False, tol=1e-4, store_basis=True)
     with pytest.raises(Exception, match="Lanczos record"):
