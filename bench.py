@@ -1,7 +1,9 @@
 """Throughput of the hypergradient hot path on the 64-pair batch workload.
 
 One step = one outer iteration over the batch (64 training pairs of uneven sizes, FoE with
-16 5x5 filters): warm-started lower solve (L-BFGS), recycle refresh, warm-started recycled-CG
+16 5x5 filters): warm-started lower solve (L-BFGS), recycle refresh (by default the inner variant
+of eq. (3.4), projected with the previous system's Hessian through its CG Lanczos record),
+warm-started recycled-CG
 Hessian solve, J w contraction, then an Adam update of theta (Section 5.2).  The metric is
 hypergradients per second at a stopping tolerance that keeps every hypergradient within 1e-4
 relative error of a tight reference solve (checked after the timed region and reported).
@@ -325,7 +327,7 @@ def main():
     ap.add_argument("--workload", default="batch64", choices=["batch64", "inpaint"],
                     help="batch64: the 64-pair deconvolution batch (the metric's workload); inpaint: 1024 "
                          "inpainting pairs shaped like the paper's Section 5.1 experiment")
-    ap.add_argument("--refresh", default="outer", choices=["outer", "inner"],
+    ap.add_argument("--refresh", default="inner", choices=["outer", "inner"],
                     help="recycle refresh: outer (eq. (3.3), current Hessian) or inner (eq. (3.4), the last "
                          "solve's Hessian through its Lanczos record; CG only)")
     ap.add_argument("--method", default="cg", choices=["cg", "minres"],
