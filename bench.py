@@ -268,14 +268,14 @@ def gpu_arm(args, rank, world, dist):
 # ---------------------------------------------------------------------------------------------
 # CPU checker arm (bounded sample)
 
-def oracle_sample(steps, warmup, max_seconds=None, strategy="RGen-L(R)", workload="batch64"):
-    """Run the FP64 checker on the smallest pair of the batch for warmup + steps outer steps.
-    Returns (seconds per timed step, sample description)."""
+def oracle_sample(steps, warmup, max_seconds=None, strategy="RGen-L(R)", workload="batch64", variant="inner"):
+    """Run the FP64 checker on the smallest pair of the batch for warmup + steps outer steps, with
+    the same refresh variant as the GPU arm.  Returns (seconds per timed step, sample description)."""
     from paper_2412_08264_gb300 import synth
     from paper_2412_08264_gb300.strategy import parse
     from oracle.bilevel import BilevelProblem, Adam
     from oracle.krylov import rcg
-    from oracle.recycle import refresh
+    from oracle.recycle import refresh, refresh_inner
 
     wl, s_rec, _ = make_workload(workload)
     k0 = min(range(len(wl.pairs)), key=lambda k: wl.pairs[k].height * wl.pairs[k].width)
@@ -288,6 +288,7 @@ def oracle_sample(steps, warmup, max_seconds=None, strategy="RGen-L(R)", workloa
     x = np.zeros((ll.h, ll.w))
     w = np.zeros(ll.n)
     U = C = V = None
+    AH_prev = None
     times = []
     g0 = np.linalg.norm(ll.grad(np.zeros_like(x), theta))
     for i in range(warmup + steps):
@@ -297,11 +298,17 @@ def oracle_sample(steps, warmup, max_seconds=None, strategy="RGen-L(R)", workloa
         AH = prob.apply_H(0, x, theta)
         if st.recycles and V is not None:
             Up = U if U is not None else np.zeros((ll.n, 0))
-            U, C, Z, _ = refresh(Up, V, AH, lambda v: prob.Jw(0, x, theta, v), s_rec, st.kind, st.size, st.side)
+            Jfun = lambda v: prob.Jw(0, x, theta, v)   # noqa: E731
+            if variant == "inner":
+                U, C, Z, _ = refresh_inner(Up, V, AH_prev, AH, Jfun, s_rec, st.kind, st.size, st.side)
+            else:
+                U, C, Z, _ = refresh(Up, V, AH, Jfun, s_rec, st.kind, st.size, st.side)
         g = prob.rhs(0, x)
         out = rcg(AH, g, w, U, C, tol=(INPAINT_RTOL if workload == "inpaint" else RTOL) * np.linalg.norm(g),
-                  maxit=3000, kmax_store=MAX_BASIS)
-        w, V = out["w"], out["V"]
+                  maxit=3000, kmax_store=None if variant == "inner" else MAX_BASIS)
+        # inner: the first max_basis - 1 residuals (the Lanczos record); outer: the most recent max_basis
+        w, V = out["w"], (out["V"][:, :MAX_BASIS - 1] if variant == "inner" else out["V"])
+        AH_prev = AH
         hg = prob.Jw(0, x, theta, w)
         theta = opt.step(theta, hg)
         dt = time.perf_counter() - t0
@@ -310,7 +317,7 @@ def oracle_sample(steps, warmup, max_seconds=None, strategy="RGen-L(R)", workloa
         if max_seconds is not None and sum(times) > max_seconds and len(times) >= 1:
             break
     desc = (f"pair {k0} of the {workload} batch ({ll.h}x{ll.w}, {wl.n_filters} {wl.filter_size}x{wl.filter_size} "
-            f"filters), {strategy}, "
+            f"filters), {strategy} ({variant} refresh), "
             f"{warmup} warm-up + {len(times)} timed outer steps, FP64 NumPy")
     return float(np.mean(times)), len(times), desc
 
@@ -356,7 +363,8 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        sec, n, desc = oracle_sample(args.steps, args.warmup, strategy=args.strategy, workload=args.workload)
+        sec, n, desc = oracle_sample(args.steps, args.warmup, strategy=args.strategy, workload=args.workload,
+                                     variant=args.refresh)
         v = 1.0 / sec
         print(json.dumps({"impl": "reference", "metric": metric, "value": v, "unit": "hypergradients/s",
                           "n_gpus": args.gpus, "steps": n, "warmup": args.warmup, "ms_per_step": sec * 1e3,
@@ -450,7 +458,8 @@ def main():
         line["e2e"] = {"value": K * world * args.steps / (ms_e / 1e3), "unit": "hypergradients/s",
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": wl.n_params * 8}
     if rank == 0 and world == 1 and args.cpu_baseline:
-        sec, n, desc = oracle_sample(2, 1, max_seconds=30.0, strategy=args.strategy, workload=args.workload)
+        sec, n, desc = oracle_sample(2, 1, max_seconds=30.0, strategy=args.strategy, workload=args.workload,
+                                     variant=args.refresh)
         line["cpu_baseline"] = {"value": 1.0 / sec, "unit": "hypergradients/s", "cores": os.cpu_count(),
                                 "kind": "oracle", "sample": desc}
     if rank == 0:
