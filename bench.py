@@ -177,7 +177,8 @@ def gpu_arm(args, rank, world, dist):
                 y_d.copy_(y_h, non_blocking=True)
                 xs_d.copy_(xs_h, non_blocking=True)
                 P.set_data(y_d, xs_d)
-            P.lower_solve(theta_d, xhat, gtol=LOWER_GTOL, relative=True, max_iters=2000, allow_noconv=True)
+            P.lower_solve(theta_d, xhat, gtol=LOWER_GTOL, relative=True, max_iters=2000, allow_noconv=True,
+                          graph=args.graph)
             if strat.recycles and state["t"] > 0:
                 P.ritz_update(strat, s_rec, variant=args.refresh)
             info = P.hessian_solve(w, recycle=strat.recycles, nsc=strat.nsc, tol=rtol, relative=True, maxit=3000,
@@ -348,8 +349,8 @@ def main():
     ap.add_argument("--prof-steps", type=int, default=2,
                     help="extra steps timed kernel by kernel with CUDA events (roofline, kernel_ms)")
     ap.add_argument("--no-graph", dest="graph", action="store_false",
-                    help="launch the Krylov loop kernel by kernel from the host (profilers that do not "
-                         "follow conditional CUDA-graph bodies see every launch)")
+                    help="launch the Krylov and L-BFGS loops kernel by kernel from the host (profilers that "
+                         "do not follow conditional CUDA-graph bodies see every launch)")
     ap.add_argument("--profile-range", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (ncu --profile-from-start off)")
     args = ap.parse_args()

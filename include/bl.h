@@ -95,6 +95,9 @@ typedef struct {
   double armijo_slack;   /* accept Phi(x + t d) <= Phi(x) + 1e-4 t g^T d + armijo_slack |Phi(x)|:
                             0 is the plain Armijo rule; FP32 problems need about 1e-6 because FP32
                             values of Phi cannot resolve decreases below that level */
+  int32_t graph;         /* non-zero: run the iteration loop as one CUDA-graph launch (a WHILE node whose
+                            condition is set on the device); the host-polled loop is used instead while
+                            profiling is enabled */
 } bl_lbfgs_opts;
 
 /* CG / recycled CG (augmented CG on P H P, P = I - C C^T: valid for SPD Hessians) and MINRES /

@@ -41,7 +41,8 @@ class RegDesc(C.Structure):
 
 class LbfgsOpts(C.Structure):
     _fields_ = [("max_iters", C.c_int32), ("history", C.c_int32), ("gtol", C.c_double),
-                ("gtol_relative", C.c_int32), ("max_backtrack", C.c_int32), ("armijo_slack", C.c_double)]
+                ("gtol_relative", C.c_int32), ("max_backtrack", C.c_int32), ("armijo_slack", C.c_double),
+                ("graph", C.c_int32)]
 
 
 class KrylovOpts(C.Structure):

@@ -114,14 +114,14 @@ class Problem:
 
     def lower_solve(self, theta: torch.Tensor, xhat: torch.Tensor, pairs=None, gtol: float = 1e-5,
                     relative: bool = True, max_iters: int = 5000, history: int = 10, max_backtrack: int = 30,
-                    armijo_slack: Optional[float] = None, allow_noconv: bool = False):
+                    armijo_slack: Optional[float] = None, allow_noconv: bool = False, graph: bool = True):
         pa, n, idx = self._pairs(pairs)
         self._check_theta(theta)
         self._check_images(xhat, idx)
         if armijo_slack is None:
             armijo_slack = 1e-6 if self.dtype == torch.float32 else 0.0
         opts = L.LbfgsOpts(int(max_iters), int(history), float(gtol), 1 if relative else 0, int(max_backtrack),
-                           float(armijo_slack))
+                           float(armijo_slack), 1 if graph else 0)
         info = (L.SolveInfo * n)()
         allow = (L.BL_OK, L.BL_ENOCONV) if allow_noconv else (L.BL_OK,)
         L.check(self.lib.bl_lower_solve(self.h, pa, n, _ptr(theta), C.byref(opts), _ptr(xhat), info),

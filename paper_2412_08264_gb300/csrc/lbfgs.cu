@@ -509,7 +509,7 @@ static bl_status lbfgs_impl(bl_problem* P, const std::vector<int>& mask_host, co
   };
   // every accepted step takes at most max_bt body runs
   const long long cap = (long long)o->max_iters * max_bt + 1;
-  bool use_graph = *P->h_flag > 0 && !P->prof && !P->graph_failed;
+  bool use_graph = *P->h_flag > 0 && o->graph && !P->prof && !P->graph_failed;
   if (use_graph) {
     const LbfgsGraphKey key{P->cpart, P->tpart, P->S, MH, max_bt, o->max_iters, o->armijo_slack};
     if (!P->lgraph || !(P->lgraph_key == key)) {
