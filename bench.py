@@ -41,9 +41,9 @@ ADAM_LR = 1e-2
 FP32_FMA_LANES = 152 * 128   # GB300: 152 SMs x 128 FP32 lanes
 # DRAM bytes (read + write) per pixel of one fused Hessian action with the recycled-CG dots over
 # 16 recycle columns, from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum on the
-# first 16 pairs of the batch: 179.4 MB for 1,306,624 px; summary in
+# first 16 pairs of the batch: 179.3 MB for 1,306,624 px; summary in
 # profiles/hvp_k_foe_stencil_f5_batch16.md), scaled to a launch by the pixels it processes.
-HVP_DRAM_BYTES_PER_PIXEL = 137.4
+HVP_DRAM_BYTES_PER_PIXEL = 137.2
 
 
 def hvp_flops_per_pixel(n_filters, f, rb, masked=False):
