@@ -123,6 +123,10 @@ def make_workload(name, replica=0):
         wl = synth.inpaint_batch(seed=replica)
         return wl, 30, (f"inpaint1024x28_n3f5: {len(wl.pairs)} pairs of 28x28, 30 % of pixels measured, "
                         f"noise 0.1, 3 5x5 filters, phi = s^2, p={wl.n_params}")
+    if name == "deconv":
+        wl = synth.deconv_batch(seed=replica)
+        return wl, 16, (f"deconv512x64_n24f5: {len(wl.pairs)} pairs of 64x64, 9x9 blur sigma 3, noise 0.08, "
+                        f"24 5x5 DCT-initialised filters, phi = log(1 + s^2), p={wl.n_params}")
     wl = synth.batch_64(replica=replica)
     return wl, S_RECYCLE, None
 
@@ -332,9 +336,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--strategy", default="RGen-L(R)")
-    ap.add_argument("--workload", default="batch64", choices=["batch64", "inpaint"],
+    ap.add_argument("--workload", default="batch64", choices=["batch64", "inpaint", "deconv"],
                     help="batch64: the 64-pair deconvolution batch (the metric's workload); inpaint: 1024 "
-                         "inpainting pairs shaped like the paper's Section 5.1 experiment")
+                         "inpainting pairs shaped like the paper's Section 5.1 experiment; deconv: 512 "
+                         "64x64 pairs shaped like its Section 5.2 experiment (use --method minres)")
     ap.add_argument("--refresh", default="inner", choices=["outer", "inner"],
                     help="recycle refresh: outer (eq. (3.3), current Hessian) or inner (eq. (3.4), the last "
                          "solve's Hessian through its Lanczos record; CG only)")
@@ -355,6 +360,8 @@ def main():
                     help="bracket the timed steps with cudaProfilerStart/Stop (ncu --profile-from-start off)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
+    if args.method == "minres":
+        args.refresh = "outer"      # the Lanczos record of the inner refresh is kept by CG solves
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -371,8 +378,8 @@ def main():
                           "n_gpus": args.gpus, "steps": n, "warmup": args.warmup, "ms_per_step": sec * 1e3,
                           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                           "data": "synthetic",
-                          "config": {"workload": ("batch64_foe_n16f5" if args.workload == "batch64"
-                                                  else "inpaint1024x28_n3f5") + " (sample)",
+                          "config": {"workload": {"batch64": "batch64_foe_n16f5", "inpaint": "inpaint1024x28_n3f5",
+                                                  "deconv": "deconv512x64_n24f5"}[args.workload] + " (sample)",
                                      "strategy": args.strategy},
                           "cpu_baseline": {"value": v, "unit": "hypergradients/s", "cores": os.cpu_count(),
                                            "kind": "oracle", "sample": desc},

@@ -15,7 +15,8 @@ painted in order over a zero background, each with a value U[0, 1].
 
 Filter initialisation (Section 5, eq. (5.1) parametrisation): per filter
 one log-weight alpha_j = -3 followed by f*f taps drawn N(0, 0.1^2) and made
-zero-mean once.  theta = [alpha_1, taps_1, ..., alpha_N, taps_N].
+zero-mean once (the deconvolution workload uses the non-constant DCT basis
+filters instead, as Section 5.2 does).  theta = [alpha_1, taps_1, ..., alpha_N, taps_N].
 """
 from __future__ import annotations
 
@@ -186,6 +187,40 @@ def uneven_foe(sizes, n_filters: int = 4, f: int = 5, blur_radius: int = 4, seed
     return _fill(wl, data_ss)
 
 
+def dct_filters(n_filters: int, f: int) -> np.ndarray:
+    """The non-constant 2-D DCT-II basis filters of size f x f (unit l2 norm), ordered by frequency
+    pair (u, v) row-major, (0, 0) left out: Section 5.2 initialises the FoE filters with them."""
+    out = []
+    a = np.arange(f)
+    for u in range(f):
+        for v in range(f):
+            if u == 0 and v == 0:
+                continue
+            k = np.outer(np.cos(np.pi * (2 * a + 1) * u / (2 * f)), np.cos(np.pi * (2 * a + 1) * v / (2 * f)))
+            out.append(k / np.linalg.norm(k))
+    if n_filters > len(out):
+        raise ValueError("more filters than non-constant DCT basis functions")
+    return np.stack(out[:n_filters])
+
+
+def deconv_batch(n_pairs: int = 512, side: int = 64, blur_sigma: float = 3.0, blur_radius: int = 4,
+                 noise_sigma: float = 0.08, n_filters: int = 24, f: int = 5, seed: int = 0) -> Workload:
+    """Deconvolution pairs shaped like Section 5.2's experiment (512 crops of 64 x 64, Gaussian blur
+    sigma 3 truncated to 9 x 9, noise, 24 learned 5 x 5 filters with phi = log(1 + s^2), the filters
+    initialised with the non-constant DCT basis and alpha_j = -3)."""
+    pairs = [PairSpec(side, side, blur_sigma, blur_radius, noise_sigma)] * n_pairs
+    wl = Workload(f"deconv{n_pairs}x{side}_n{n_filters}f{f}", pairs, reg="foe", n_filters=n_filters,
+                  filter_size=f, phi="log1p", recycle_dim=16)
+    wl = _fill(wl, np.random.SeedSequence([ROOT_SEED, 19, seed]))
+    taps = dct_filters(n_filters, f)
+    theta = np.empty(n_filters * (f * f + 1))
+    for j in range(n_filters):
+        theta[j * (f * f + 1)] = -3.0
+        theta[j * (f * f + 1) + 1:(j + 1) * (f * f + 1)] = taps[j].ravel()
+    wl.theta0 = theta
+    return wl
+
+
 def inpaint_batch(n_pairs: int = 1024, side: int = 28, keep: float = 0.3, noise_sigma: float = 0.1,
                   n_filters: int = 3, f: int = 5, seed: int = 0) -> Workload:
     """Inpainting pairs shaped like Section 5.1's experiment (28 x 28 images, 30 % of the pixels
@@ -203,6 +238,7 @@ WORKLOADS = {
     "batch8_1024_foe_n24f7": batch_1024,
     "large2048_foe_n48f7": large_2048,
     "inpaint1024x28_n3f5": inpaint_batch,
+    "deconv512x64_n24f5": deconv_batch,
 }
 
 

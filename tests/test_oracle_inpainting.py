@@ -106,3 +106,14 @@ def test_masked_hypergradient_fd(rng):
         hh = 1e-5
         fd = (loss(th + hh * d) - loss(th - hh * d)) / (2 * hh)
         assert abs(fd - hg @ d) < 1e-6 * max(1.0, abs(hg @ d))
+
+
+def test_dct_filters_are_an_orthonormal_zero_mean_basis():
+    """The 24 non-constant 5 x 5 DCT-II filters of the deconvolution workload: orthonormal, zero
+    mean, and with the constant filter they span all 5 x 5 filters."""
+    from paper_2412_08264_gb300 import synth
+    B = synth.dct_filters(24, 5).reshape(24, 25)
+    np.testing.assert_allclose(B @ B.T, np.eye(24), atol=1e-12)
+    np.testing.assert_allclose(B.sum(axis=1), 0.0, atol=1e-12)
+    full = np.vstack([np.full(25, 0.2), B])
+    assert np.linalg.matrix_rank(full) == 25
