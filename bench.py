@@ -36,6 +36,7 @@ S_RECYCLE = 16         # recycle dimension of the 64-pair batch (30 for the inpa
 MAX_BASIS = 32
 RTOL = 1e-4            # residual stopping tolerance (relative to ||g||)
 INPAINT_RTOL = 1e-5
+DECONV_RTOL = 1e-5
 LOWER_GTOL = 1e-5      # lower-level gradient tolerance (relative to ||grad Phi(0)||)
 ADAM_LR = 1e-2
 FP32_FMA_LANES = 152 * 128   # GB300: 152 SMs x 128 FP32 lanes
@@ -113,11 +114,15 @@ class Clocks:
 # ---------------------------------------------------------------------------------------------
 # Workloads
 
+def workload_rtol(name):
+    return {"inpaint": INPAINT_RTOL, "deconv": DECONV_RTOL}.get(name, RTOL)
+
+
 def make_workload(name, replica=0):
     """(workload, recycle dimension, description) for --workload.  The residual tolerance that
-    keeps every hypergradient within 1e-4 is RTOL for the batch and INPAINT_RTOL for the
-    inpainting pairs (70 % unmeasured pixels make their Hessians ill-conditioned: rtol 1e-4 left
-    errors of 2-3e-4)."""
+    keeps every hypergradient within 1e-4 is RTOL for the batch, INPAINT_RTOL for the inpainting
+    pairs (70 % unmeasured pixels make their Hessians ill-conditioned: rtol 1e-4 left errors of
+    2-3e-4) and DECONV_RTOL for the 64x64 deconvolution pairs (rtol 1e-4 left 1.1-1.4e-4)."""
     from paper_2412_08264_gb300 import synth
     if name == "inpaint":
         wl = synth.inpaint_batch(seed=replica)
@@ -143,7 +148,7 @@ def gpu_arm(args, rank, world, dist):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     wl, s_rec, wdesc = make_workload(args.workload, replica=rank)
-    rtol = INPAINT_RTOL if args.workload == "inpaint" else RTOL
+    rtol = workload_rtol(args.workload)
     if args.pairs and args.pairs < len(wl.pairs):
         wl.pairs, wl.x_star, wl.noise = wl.pairs[:args.pairs], wl.x_star[:args.pairs], wl.noise[:args.pairs]
     K = len(wl.pairs)
@@ -235,10 +240,11 @@ def gpu_arm(args, rank, world, dist):
         ck = clocks.stop()
         val = {}
         if validate:
-            # tight reference at the last step's point: plain CG to rtol 1e-7 from the computed w
+            # tight reference at the last step's point: the plain method (CG, or MINRES for Hessians
+            # that may be indefinite) to rtol 1e-7 from the computed w
             wref = w.clone()
             P.hessian_solve(wref, recycle=False, tol=1e-7, relative=True, maxit=6000, store_basis=False,
-                            warm_start=True, allow_noconv=True)
+                            warm_start=True, allow_noconv=True, method=args.method)
             _, per_ref = P.hypergrad(wref, per_pair=True)
             err = (per - per_ref).norm(dim=1) / per_ref.norm(dim=1)
             mean_err = float((per.mean(0) - per_ref.mean(0)).norm() / per_ref.mean(0).norm())
@@ -273,13 +279,15 @@ def gpu_arm(args, rank, world, dist):
 # ---------------------------------------------------------------------------------------------
 # CPU checker arm (bounded sample)
 
-def oracle_sample(steps, warmup, max_seconds=None, strategy="RGen-L(R)", workload="batch64", variant="inner"):
+def oracle_sample(steps, warmup, max_seconds=None, strategy="RGen-L(R)", workload="batch64", variant="inner",
+                  method="cg"):
     """Run the FP64 checker on the smallest pair of the batch for warmup + steps outer steps, with
-    the same refresh variant as the GPU arm.  Returns (seconds per timed step, sample description)."""
+    the same refresh variant and Krylov method as the GPU arm.  Returns (seconds per timed step,
+    sample description)."""
     from paper_2412_08264_gb300 import synth
     from paper_2412_08264_gb300.strategy import parse
     from oracle.bilevel import BilevelProblem, Adam
-    from oracle.krylov import rcg
+    from oracle.krylov import rcg, rminres
     from oracle.recycle import refresh, refresh_inner
 
     wl, s_rec, _ = make_workload(workload)
@@ -309,8 +317,12 @@ def oracle_sample(steps, warmup, max_seconds=None, strategy="RGen-L(R)", workloa
             else:
                 U, C, Z, _ = refresh(Up, V, AH, Jfun, s_rec, st.kind, st.size, st.side)
         g = prob.rhs(0, x)
-        out = rcg(AH, g, w, U, C, tol=(INPAINT_RTOL if workload == "inpaint" else RTOL) * np.linalg.norm(g),
-                  maxit=3000, kmax_store=None if variant == "inner" else MAX_BASIS)
+        tol = workload_rtol(workload) * np.linalg.norm(g)
+        if method == "minres":
+            out = rminres(AH, g, w, U, C, tol=tol, maxit=3000)
+            out["V"] = out["V"][:, -MAX_BASIS:]
+        else:
+            out = rcg(AH, g, w, U, C, tol=tol, maxit=3000, kmax_store=None if variant == "inner" else MAX_BASIS)
         # inner: the first max_basis - 1 residuals (the Lanczos record); outer: the most recent max_basis
         w, V = out["w"], (out["V"][:, :MAX_BASIS - 1] if variant == "inner" else out["V"])
         AH_prev = AH
@@ -322,7 +334,7 @@ def oracle_sample(steps, warmup, max_seconds=None, strategy="RGen-L(R)", workloa
         if max_seconds is not None and sum(times) > max_seconds and len(times) >= 1:
             break
     desc = (f"pair {k0} of the {workload} batch ({ll.h}x{ll.w}, {wl.n_filters} {wl.filter_size}x{wl.filter_size} "
-            f"filters), {strategy} ({variant} refresh), "
+            f"filters), {strategy} ({variant} refresh, {'MINRES' if method == 'minres' else 'CG'}), "
             f"{warmup} warm-up + {len(times)} timed outer steps, FP64 NumPy")
     return float(np.mean(times)), len(times), desc
 
@@ -372,7 +384,7 @@ def main():
         if rank != 0:
             return
         sec, n, desc = oracle_sample(args.steps, args.warmup, strategy=args.strategy, workload=args.workload,
-                                     variant=args.refresh)
+                                     variant=args.refresh, method=args.method)
         v = 1.0 / sec
         print(json.dumps({"impl": "reference", "metric": metric, "value": v, "unit": "hypergradients/s",
                           "n_gpus": args.gpus, "steps": n, "warmup": args.warmup, "ms_per_step": sec * 1e3,
@@ -429,7 +441,7 @@ def main():
         "config": {"workload": out["wdesc"] or (f"batch64_foe_n16f5: {K} pairs, sides 128-512, {n_pix} px, "
                                                 f"16 5x5 filters, 9x9 blur, p={wl.n_params}"),
                    "strategy": out["strategy"].acronym(), "refresh": args.refresh, "krylov": args.method, "recycle_dim": out["s_rec"], "max_basis": args.max_basis,
-                   "stop": f"residual rtol {INPAINT_RTOL if args.workload == 'inpaint' else RTOL}", "lower_gtol_rel": LOWER_GTOL, "outer": "Adam lr 1e-2",
+                   "stop": f"residual rtol {workload_rtol(args.workload)}", "lower_gtol_rel": LOWER_GTOL, "outer": "Adam lr 1e-2",
                    "l2": "inputs larger than L2 (batch working set > 1 GB), no flush"},
         "hg_rel_err_max": rec.get("hg_err_max"), "hg_rel_err_mean_grad": rec.get("hg_err_mean_grad"),
         "krylov_iters_per_step": [int(np.max(it)) for it in rec["iters"]],
@@ -467,7 +479,7 @@ def main():
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": wl.n_params * 8}
     if rank == 0 and world == 1 and args.cpu_baseline:
         sec, n, desc = oracle_sample(2, 1, max_seconds=30.0, strategy=args.strategy, workload=args.workload,
-                                     variant=args.refresh)
+                                     variant=args.refresh, method=args.method)
         line["cpu_baseline"] = {"value": 1.0 / sec, "unit": "hypergradients/s", "cores": os.cpu_count(),
                                 "kind": "oracle", "sample": desc}
     if rank == 0:

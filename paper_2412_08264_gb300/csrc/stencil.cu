@@ -1039,7 +1039,8 @@ static bl_status prepare_one(bl_problem* P) {
   BL_CUDA_TRY(cudaFuncSetAttribute(k_foe_stencil<T, F, kModeHvp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   BL_CUDA_TRY(cudaFuncSetAttribute(k_foe_stencil<T, F, kModeGrad>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   constexpr int RS = tile_out(F) + 2 * (F / 2);
-  const size_t smj = (2 * (size_t)RS * RS + 2 * 16 * kStencilThreads + (size_t)(F * F + 1) * kStencilThreads) * sizeof(T);
+  const size_t smj = (2 * (size_t)RS * jw_pitch<T>(RS) + 2 * 16 * kStencilThreads +
+                      (size_t)(F * F + 1) * kStencilThreads) * sizeof(T);
   BL_CUDA_TRY(cudaFuncSetAttribute(k_foe_jw<T, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smj));
   return BL_OK;
 }
