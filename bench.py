@@ -148,7 +148,7 @@ def gpu_arm(args, rank, world, dist):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     wl, s_rec, wdesc = make_workload(args.workload, replica=rank)
-    rtol = workload_rtol(args.workload)
+    rtol = args.rtol or workload_rtol(args.workload)
     if args.pairs and args.pairs < len(wl.pairs):
         wl.pairs, wl.x_star, wl.noise = wl.pairs[:args.pairs], wl.x_star[:args.pairs], wl.noise[:args.pairs]
     K = len(wl.pairs)
@@ -165,7 +165,7 @@ def gpu_arm(args, rank, world, dist):
     n_pix = xs.numel()
     strategy = parse(args.strategy)
 
-    def run(strat, steps, warmup, e2e=False, validate=False, profile_range=False, prof_steps=0):
+    def run(strat, steps, warmup, e2e=False, validate=False, profile_range=False, prof_steps=0, warm=True):
         P = api.from_workload(wl, y, xs, max_recycle=s_rec, max_basis=args.max_basis)
         y_d = torch.empty_like(y)
         xs_d = torch.empty_like(xs)
@@ -192,7 +192,7 @@ def gpu_arm(args, rank, world, dist):
                 P.ritz_update(strat, s_rec, variant=args.refresh)
             info = P.hessian_solve(w, recycle=strat.recycles, nsc=strat.nsc, tol=rtol, relative=True, maxit=3000,
                                    store_basis=(("lanczos" if args.refresh == "inner" else True)
-                                                if strat.recycles else False), warm_start=True,
+                                                if strat.recycles else False), warm_start=warm,
                                    nsc_scale=None if hg_prev is None else [hg_prev] * K, allow_noconv=True,
                                    method=args.method, graph=args.graph)
             mean, per = P.hypergrad(w, per_pair=True)
@@ -272,15 +272,17 @@ def gpu_arm(args, rank, world, dist):
               prof_steps=args.prof_steps)
     cg = (run(parse("none"), args.steps, args.warmup, validate=True, prof_steps=args.prof_steps)
           if (args.compare_cg and strategy.recycles) else None)
+    cold = (run(parse("none"), args.steps, args.warmup, validate=True, warm=False)
+            if (args.compare_cg and args.cold and strategy.recycles) else None)
     e2e = run(strategy, args.steps, args.warmup, e2e=True) if args.e2e else None
-    return dict(rec=rec, cg=cg, e2e=e2e, K=K, n_pix=n_pix, wl=wl, strategy=strategy, s_rec=s_rec, wdesc=wdesc)
+    return dict(rec=rec, cg=cg, cold=cold, e2e=e2e, K=K, n_pix=n_pix, wl=wl, strategy=strategy, s_rec=s_rec, wdesc=wdesc)
 
 
 # ---------------------------------------------------------------------------------------------
 # CPU checker arm (bounded sample)
 
 def oracle_sample(steps, warmup, max_seconds=None, strategy="RGen-L(R)", workload="batch64", variant="inner",
-                  method="cg"):
+                  method="cg", rtol=0.0):
     """Run the FP64 checker on the smallest pair of the batch for warmup + steps outer steps, with
     the same refresh variant and Krylov method as the GPU arm.  Returns (seconds per timed step,
     sample description)."""
@@ -317,7 +319,7 @@ def oracle_sample(steps, warmup, max_seconds=None, strategy="RGen-L(R)", workloa
             else:
                 U, C, Z, _ = refresh(Up, V, AH, Jfun, s_rec, st.kind, st.size, st.side)
         g = prob.rhs(0, x)
-        tol = workload_rtol(workload) * np.linalg.norm(g)
+        tol = (rtol or workload_rtol(workload)) * np.linalg.norm(g)
         if method == "minres":
             out = rminres(AH, g, w, U, C, tol=tol, maxit=3000)
             out["V"] = out["V"][:, -MAX_BASIS:]
@@ -360,6 +362,10 @@ def main():
     ap.add_argument("--max-basis", type=int, default=MAX_BASIS,
                     help="Krylov basis vectors kept per pair for the next refresh")
     ap.add_argument("--no-compare-cg", dest="compare_cg", action="store_false")
+    ap.add_argument("--no-cold", dest="cold", action="store_false",
+                    help="skip the cold-started plain solve (w_0 = 0 for every system)")
+    ap.add_argument("--rtol", type=float, default=0.0,
+                    help="residual stopping tolerance relative to ||g|| (default: the workload's)")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--pairs", type=int, default=0, help="use only the first PAIRS pairs (profiling cases)")
@@ -384,7 +390,7 @@ def main():
         if rank != 0:
             return
         sec, n, desc = oracle_sample(args.steps, args.warmup, strategy=args.strategy, workload=args.workload,
-                                     variant=args.refresh, method=args.method)
+                                     variant=args.refresh, method=args.method, rtol=args.rtol)
         v = 1.0 / sec
         print(json.dumps({"impl": "reference", "metric": metric, "value": v, "unit": "hypergradients/s",
                           "n_gpus": args.gpus, "steps": n, "warmup": args.warmup, "ms_per_step": sec * 1e3,
@@ -441,7 +447,7 @@ def main():
         "config": {"workload": out["wdesc"] or (f"batch64_foe_n16f5: {K} pairs, sides 128-512, {n_pix} px, "
                                                 f"16 5x5 filters, 9x9 blur, p={wl.n_params}"),
                    "strategy": out["strategy"].acronym(), "refresh": args.refresh, "krylov": args.method, "recycle_dim": out["s_rec"], "max_basis": args.max_basis,
-                   "stop": f"residual rtol {workload_rtol(args.workload)}", "lower_gtol_rel": LOWER_GTOL, "outer": "Adam lr 1e-2",
+                   "stop": f"residual rtol {args.rtol or workload_rtol(args.workload)}", "lower_gtol_rel": LOWER_GTOL, "outer": "Adam lr 1e-2",
                    "l2": "inputs larger than L2 (batch working set > 1 GB), no flush"},
         "hg_rel_err_max": rec.get("hg_err_max"), "hg_rel_err_mean_grad": rec.get("hg_err_mean_grad"),
         "krylov_iters_per_step": [int(np.max(it)) for it in rec["iters"]],
@@ -472,6 +478,12 @@ def main():
                             "kernel_ms": ({k: round(v["ms"], 3) for k, v in cg["prof"].items()} if cg["prof"] else None),
                             "hvp_avg_launch_ms": (cg["prof"]["hvp"]["ms"] / max(1, cg["prof"]["hvp"]["launches"])
                                                   if cg["prof"] else None)}
+    if out["cold"] is not None:
+        cold = out["cold"]
+        ms_c = tmax(cold["ms"])
+        line["plain_cg_cold"] = {"value": K * world * args.steps / (ms_c / 1e3), "ms_per_step": ms_c / args.steps,
+                                 "krylov_iters_total": int(np.sum(cold["iters"])),
+                                 "hg_rel_err_max": cold.get("hg_err_max")}
     if out["e2e"] is not None:
         ms_e = tmax(out["e2e"]["ms"])
         h2d = 2 * n_pix * 4 + wl.n_params * 8
@@ -479,7 +491,7 @@ def main():
                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": wl.n_params * 8}
     if rank == 0 and world == 1 and args.cpu_baseline:
         sec, n, desc = oracle_sample(2, 1, max_seconds=30.0, strategy=args.strategy, workload=args.workload,
-                                     variant=args.refresh, method=args.method)
+                                     variant=args.refresh, method=args.method, rtol=args.rtol)
         line["cpu_baseline"] = {"value": 1.0 / sec, "unit": "hypergradients/s", "cores": os.cpu_count(),
                                 "kind": "oracle", "sample": desc}
     if rank == 0:
