@@ -47,6 +47,16 @@ constexpr int kMaxTM = 96;                // max columns of W (recycle + basis)
 constexpr int kMaxHistory = 16;           // L-BFGS memory
 
 __host__ __device__ constexpr int tile_out(int F) { return (kTileRegion - 2 * (F / 2)) & ~3; }
+// Output side of the J w tiles.  J w has no step-1 region to fit in 64 x 64 (its K_j w is computed
+// per 4 x 4 block straight from the staged tile), so FP32 takes the full 16 x 16 grid of 4 x 4
+// blocks: one tile covers a 64 x 64 image.  FP64 keeps the stencil's tile (its 7 x 7 shared-memory
+// budget has no room for a wider staged region).
+template <typename T>
+__host__ __device__ constexpr int jw_tile_out(int F) { return sizeof(T) == 4 ? 64 : tile_out(F); }
+// Which work-list a per-pair reduction of unit partials walks.
+constexpr int kUnitChunks = 0;
+constexpr int kUnitTiles = 1;
+constexpr int kUnitJwTiles = 2;
 
 struct PairDev {
   int h, w;
@@ -54,6 +64,7 @@ struct PairDev {
   const unsigned char* opm;   // inpainting: this pair's measured-pixel mask (A = diag(opm != 0)); null: blur
   int rb;
   int tbeg, tend;      // tiles [tbeg, tend) of this pair
+  int jtbeg, jtend;    // J w tiles [jtbeg, jtend)
   int cbeg, cend;      // chunks [cbeg, cend)
   float gf[2 * BL_MAX_BLUR_RADIUS + 1];
   double gd[2 * BL_MAX_BLUR_RADIUS + 1];
@@ -119,7 +130,7 @@ struct PairHost {
   int rb;
   double sigma;
   bool masked;
-  int tbeg, tend, cbeg, cend;
+  int tbeg, tend, cbeg, cend, jtbeg, jtend;
 };
 
 }  // namespace bl
@@ -135,11 +146,12 @@ struct bl_problem {
   long long n_tot = 0;
   cudaStream_t stream = nullptr;
   int64_t launches = 0;
-  int n_tiles = 0, n_chunks = 0;
+  int n_tiles = 0, n_chunks = 0, n_jtiles = 0;
   bool vec4 = false;                // every pair's n is a multiple of 4 (16-byte column starts)
 
   bl::PairDev* d_pairs = nullptr;
   bl::TileDev* d_tiles = nullptr;
+  bl::TileDev* d_jtiles = nullptr;         // the J w work-list (tiles of jw_tile_out)
   bl::ChunkDev* d_chunks = nullptr;
 
   void *y = nullptr, *xstar = nullptr, *xhat = nullptr;
@@ -268,7 +280,7 @@ bl_status run_lower_solve(bl_problem* P, const std::vector<int>& mask_host, cons
 // ---- vec.cu: batched vector helpers ----
 // Sum per-unit partials (units = tiles or chunks; layout part[(col * n_units + u) * ncomp + m])
 // over the units of each pair: out[(k * cols + col) * ncomp + m].
-bl_status reduce_units(bl_problem* P, const double* part, int ncomp, int cols, bool tiles, const int* mask,
+bl_status reduce_units(bl_problem* P, const double* part, int ncomp, int cols, int units, const int* mask,
                        const int* colcnt, double* out);
 // Reduce per-chunk partials: out[k * ncomp + c] = sum over chunks of pair k (masked pairs only).
 bl_status reduce_chunk_partials(bl_problem* P, int ncomp, const int* mask, double* out);

@@ -174,7 +174,7 @@ void bl_problem_destroy(bl_problem* P) {
   cudaStreamSynchronize(P->stream);
   destroy_krylov_graph(P);
   if (P->cstream) cudaStreamDestroy(P->cstream);
-  void* bufs[] = {P->d_pairs, P->d_tiles, P->d_chunks, P->y, P->xstar, P->xhat, P->fu, P->fd, P->theta,
+  void* bufs[] = {P->d_pairs, P->d_tiles, P->d_jtiles, P->d_chunks, P->y, P->xstar, P->xhat, P->fu, P->fd, P->theta,
                   P->taps_f, P->taps_d, P->ealpha, P->r, P->pv, P->q, P->w, P->g, P->tmp, P->U, P->C, P->Z,
                   P->V, P->W, P->Wt, P->HWt, P->st, P->c, P->zc, P->e, P->ztr, P->ztc, P->d_s, P->d_hasz,
                   P->d_active, P->d_cols, P->d_flag, P->dG, P->dT, P->dJ, P->dY, P->dY2, P->dY3, P->d_tk,
@@ -240,8 +240,9 @@ bl_status bl_problem_create(const bl_pair_desc* pairs, int32_t K, const bl_reg_d
 
   // pair geometry, tiles and chunks
   const int TILE = tile_out(P->F);
+  const int TILEJ = P->prec == BL_FP32 ? jw_tile_out<float>(P->F) : jw_tile_out<double>(P->F);
   std::vector<PairDev> pd(K);
-  std::vector<TileDev> tiles;
+  std::vector<TileDev> tiles, jtiles;
   std::vector<ChunkDev> chunks;
   long long off = 0;
   for (int k = 0; k < K; ++k) {
@@ -257,6 +258,10 @@ bl_status bl_problem_create(const bl_pair_desc* pairs, int32_t K, const bl_reg_d
     for (int ty = 0; ty < ph.h; ty += TILE)
       for (int tx = 0; tx < ph.w; tx += TILE) tiles.push_back(TileDev{k, ty, tx});
     ph.tend = (int)tiles.size();
+    ph.jtbeg = (int)jtiles.size();
+    for (int ty = 0; ty < ph.h; ty += TILEJ)
+      for (int tx = 0; tx < ph.w; tx += TILEJ) jtiles.push_back(TileDev{k, ty, tx});
+    ph.jtend = (int)jtiles.size();
     ph.cbeg = (int)chunks.size();
     for (long long s = 0; s < ph.n; s += kChunk)
       chunks.push_back(ChunkDev{k, s, (int)std::min<long long>(kChunk, ph.n - s)});
@@ -271,6 +276,8 @@ bl_status bl_problem_create(const bl_pair_desc* pairs, int32_t K, const bl_reg_d
     d.rb = ph.rb;
     d.tbeg = ph.tbeg;
     d.tend = ph.tend;
+    d.jtbeg = ph.jtbeg;
+    d.jtend = ph.jtend;
     d.cbeg = ph.cbeg;
     d.cend = ph.cend;
     // 1-D normalised Gaussian; the 2-D kernel of Section 5.2 is its outer product
@@ -285,6 +292,7 @@ bl_status bl_problem_create(const bl_pair_desc* pairs, int32_t K, const bl_reg_d
   }
   P->n_tot = off;
   P->n_tiles = (int)tiles.size();
+  P->n_jtiles = (int)jtiles.size();
   P->n_chunks = (int)chunks.size();
   P->vec4 = true;
   for (const auto& ph : P->ph) P->vec4 = P->vec4 && (ph.n % 4 == 0);
@@ -306,6 +314,7 @@ bl_status bl_problem_create(const bl_pair_desc* pairs, int32_t K, const bl_reg_d
   const size_t n = (size_t)P->n_tot;
   BL_ALLOC(dalloc((void**)&P->d_pairs, K * sizeof(PairDev)));
   BL_ALLOC(dalloc((void**)&P->d_tiles, tiles.size() * sizeof(TileDev)));
+  BL_ALLOC(dalloc((void**)&P->d_jtiles, jtiles.size() * sizeof(TileDev)));
   BL_ALLOC(dalloc((void**)&P->d_chunks, chunks.size() * sizeof(ChunkDev)));
   for (void** b : {&P->y, &P->xstar, &P->xhat, &P->r, &P->pv, &P->q, &P->w, &P->g, &P->lx, &P->lg, &P->ld,
                    &P->lxt, &P->lgt})
@@ -378,6 +387,7 @@ bl_status bl_problem_create(const bl_pair_desc* pairs, int32_t K, const bl_reg_d
   e = e == cudaSuccess ? cpy(P->d_pairs, pd.data(), K * sizeof(PairDev), cudaMemcpyHostToDevice) : e;
   if (!hmask.empty()) e = e == cudaSuccess ? cpy(P->d_opmask, hmask.data(), n, cudaMemcpyHostToDevice) : e;
   e = e == cudaSuccess ? cpy(P->d_tiles, tiles.data(), tiles.size() * sizeof(TileDev), cudaMemcpyHostToDevice) : e;
+  e = e == cudaSuccess ? cpy(P->d_jtiles, jtiles.data(), jtiles.size() * sizeof(TileDev), cudaMemcpyHostToDevice) : e;
   e = e == cudaSuccess ? cpy(P->d_chunks, chunks.data(), chunks.size() * sizeof(ChunkDev), cudaMemcpyHostToDevice) : e;
   e = e == cudaSuccess ? cpy(P->y, y_packed, n * P->esz, cudaMemcpyDeviceToDevice) : e;
   e = e == cudaSuccess ? cpy(P->xstar, xstar_packed, n * P->esz, cudaMemcpyDeviceToDevice) : e;

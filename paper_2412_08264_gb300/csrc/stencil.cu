@@ -456,7 +456,7 @@ __global__ void __launch_bounds__(kStencilThreads, sizeof(T) == 4 ? 2 : 1)
 k_foe_jw(const PairDev* pairs, const TileDev* tiles, int n_tiles, const T* win, int mult,
          const int* cols, const T* xhat, const T* fu, const T* taps, const double* ealpha, int N,
          T eps, int phi, long long n_tot, const int* mask, double* tpart, int p, unsigned long long* pix) {
-  constexpr int R = F / 2, TILE = tile_out(F), RS = TILE + 2 * R;   // staged region side
+  constexpr int R = F / 2, TILE = jw_tile_out<T>(F), RS = TILE + 2 * R;   // staged region side
   constexpr int RP = jw_pitch<T>(RS);                                 // its row pitch
   constexpr int NB = TILE / 4, FF = F * F;
   const TileDev tl = tiles[blockIdx.x];
@@ -990,24 +990,24 @@ static bl_status jw_impl(bl_problem* P, const void* in, int mult, int cols, cons
                                                        P->d_cols, (const T*)P->xhat, P->ealpha,
                                                        (T)P->reg.phi_eps, mask, P->cpart);
     BL_LAUNCH_CHECK(P);
-    return reduce_units(P, P->cpart, 1, ncol, false, mask, mult ? P->d_cols : nullptr, out);
+    return reduce_units(P, P->cpart, 1, ncol, kUnitChunks, mask, mult ? P->d_cols : nullptr, out);
   }
-  bl_status st = ensure_tpart(P, (size_t)P->n_tiles * ncol * P->p);
+  bl_status st = ensure_tpart(P, (size_t)P->n_jtiles * ncol * P->p);
   if (st != BL_OK) return st;
   const T* taps = P->prec == BL_FP32 ? (const T*)(const void*)P->taps_f : (const T*)(const void*)P->taps_d;
-  dim3 grid(P->n_tiles, ncol);
+  dim3 grid(P->n_jtiles, ncol);
   ProfScope ps(P, BL_KC_JW);
   unsigned long long* pixc = pix_counter(P, BL_KC_JW);
 #define BL_JW_CASE(FF)                                                                            \
   case FF: {                                                                                      \
-    constexpr int RS = tile_out(FF) + 2 * (FF / 2);                                               \
+    constexpr int RS = jw_tile_out<T>(FF) + 2 * (FF / 2);                                         \
     size_t sm = (2 * (size_t)RS * jw_pitch<T>(RS) + 2 * 16 * kStencilThreads +                    \
                  (size_t)(FF * FF + 1) * kStencilThreads) * sizeof(T);                            \
     if (!P->capturing)                                                                            \
       BL_CUDA_TRY(cudaFuncSetAttribute(k_foe_jw<T, FF>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                        (int)sm));                                                 \
     k_foe_jw<T, FF><<<grid, kStencilThreads, sm, P->stream>>>(                                    \
-        P->d_pairs, P->d_tiles, P->n_tiles, (const T*)in, mult, P->d_cols, (const T*)P->xhat,     \
+        P->d_pairs, P->d_jtiles, P->n_jtiles, (const T*)in, mult, P->d_cols, (const T*)P->xhat,   \
         (const T*)P->fu, taps, P->ealpha, P->N, (T)P->reg.phi_eps, P->reg.phi, P->n_tot, mask,    \
         P->tpart, P->p, pixc);                                                                    \
     break;                                                                                        \
@@ -1021,7 +1021,7 @@ static bl_status jw_impl(bl_problem* P, const void* in, int mult, int cols, cons
   }
 #undef BL_JW_CASE
   BL_LAUNCH_CHECK(P);
-  return reduce_units(P, P->tpart, P->p, ncol, true, mask, mult ? P->d_cols : nullptr, out);
+  return reduce_units(P, P->tpart, P->p, ncol, kUnitJwTiles, mask, mult ? P->d_cols : nullptr, out);
 }
 
 bl_status launch_jw(bl_problem* P, const void* in, int mult, int cols, const int* mask, double* out) {
@@ -1038,7 +1038,7 @@ static bl_status prepare_one(bl_problem* P) {
   const size_t sm = StencilSmem<T, F>::bytes(P->N);
   BL_CUDA_TRY(cudaFuncSetAttribute(k_foe_stencil<T, F, kModeHvp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   BL_CUDA_TRY(cudaFuncSetAttribute(k_foe_stencil<T, F, kModeGrad>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  constexpr int RS = tile_out(F) + 2 * (F / 2);
+  constexpr int RS = jw_tile_out<T>(F) + 2 * (F / 2);
   const size_t smj = (2 * (size_t)RS * jw_pitch<T>(RS) + 2 * 16 * kStencilThreads +
                       (size_t)(F * F + 1) * kStencilThreads) * sizeof(T);
   BL_CUDA_TRY(cudaFuncSetAttribute(k_foe_jw<T, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smj));

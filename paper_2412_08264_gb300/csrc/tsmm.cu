@@ -350,7 +350,7 @@ bl_status ts_gram(bl_problem* P, const void* A, int multA, const int* colsA, int
                                                    (const double*)B, multB, colsB, mask, TM, P->cpart);
   }
   BL_LAUNCH_CHECK(P);
-  return reduce_units(P, P->cpart, TM * TM, 1, false, mask, nullptr, out);
+  return reduce_units(P, P->cpart, TM * TM, 1, kUnitChunks, mask, nullptr, out);
 }
 
 bl_status ts_gemm(bl_problem* P, const void* A, int multA, const int* colsA, int cmaxA, const double* M1, void* O1,

@@ -114,14 +114,16 @@ bl_status scatter_packed(bl_problem* P, const int32_t* pairs, int32_t npairs, co
   return BL_OK;
 }
 
-// out[(k * cols + col) * ncomp + m] = sum_{u in pair k} part[(col * n_units + u) * ncomp + m]
+// out[(k * cols + col) * ncomp + m] = sum_{u in pair k} part[(col * n_units + u) * ncomp + m]; the
+// units are the chunks, the stencil tiles or the J w tiles (kUnit*).
 __global__ void k_reduce_units(const PairDev* pairs, const double* part, int n_units, int ncomp, int cols,
-                               int tiles, const int* mask, const int* colcnt, double* out) {
+                               int units, const int* mask, const int* colcnt, double* out) {
   const int k = blockIdx.x, col = blockIdx.y;
   if (mask && !mask[k]) return;
   if (colcnt && col >= colcnt[k]) return;
   const PairDev pr = pairs[k];
-  const int beg = tiles ? pr.tbeg : pr.cbeg, end = tiles ? pr.tend : pr.cend;
+  const int beg = units == kUnitTiles ? pr.tbeg : units == kUnitJwTiles ? pr.jtbeg : pr.cbeg;
+  const int end = units == kUnitTiles ? pr.tend : units == kUnitJwTiles ? pr.jtend : pr.cend;
   for (int m = threadIdx.x; m < ncomp; m += blockDim.x) {
     double s = 0.0;
     for (int u = beg; u < end; ++u) s += part[((size_t)col * n_units + u) * ncomp + m];
@@ -129,21 +131,21 @@ __global__ void k_reduce_units(const PairDev* pairs, const double* part, int n_u
   }
 }
 
-bl_status reduce_units(bl_problem* P, const double* part, int ncomp, int cols, bool tiles, const int* mask,
+bl_status reduce_units(bl_problem* P, const double* part, int ncomp, int cols, int units, const int* mask,
                        const int* colcnt, double* out) {
-  const int n_units = tiles ? P->n_tiles : P->n_chunks;
-  k_reduce_units<<<dim3(P->K, cols), 128, 0, P->stream>>>(P->d_pairs, part, n_units, ncomp, cols,
-                                                          tiles ? 1 : 0, mask, colcnt, out);
+  const int n_units = units == kUnitTiles ? P->n_tiles : units == kUnitJwTiles ? P->n_jtiles : P->n_chunks;
+  k_reduce_units<<<dim3(P->K, cols), 128, 0, P->stream>>>(P->d_pairs, part, n_units, ncomp, cols, units, mask,
+                                                          colcnt, out);
   BL_LAUNCH_CHECK(P);
   return BL_OK;
 }
 
 bl_status reduce_chunk_partials(bl_problem* P, int ncomp, const int* mask, double* out) {
-  return reduce_units(P, P->cpart, ncomp, 1, false, mask, nullptr, out);
+  return reduce_units(P, P->cpart, ncomp, 1, kUnitChunks, mask, nullptr, out);
 }
 
 bl_status reduce_tile_partials(bl_problem* P, int ncomp, int cols, const int* mask, double* out) {
-  return reduce_units(P, P->tpart, ncomp, cols, true, mask, nullptr, out);
+  return reduce_units(P, P->tpart, ncomp, cols, kUnitTiles, mask, nullptr, out);
 }
 
 template <typename T>
