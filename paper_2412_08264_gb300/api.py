@@ -28,6 +28,12 @@ class Problem:
         """pairs: sequence of (height, width, blur_sigma, blur_radius) for blur pairs, or
         (height, width, blur_sigma, blur_radius, mask) with mask an (height, width) array of
         measured pixels (non-zero) for inpainting pairs (blur fields then ignored)."""
+        if reg not in ("tv", "foe"):
+            raise ValueError(f"unknown regulariser {reg!r} (expected 'tv' or 'foe')")
+        if precision not in ("fp32", "fp64"):
+            raise ValueError(f"unknown precision {precision!r} (expected 'fp32' or 'fp64')")
+        if phi not in L.BL_PHI:
+            raise ValueError(f"unknown phi {phi!r} (expected one of {sorted(L.BL_PHI)})")
         self.lib = L.load()
         self.K = len(pairs)
         self.sizes = [(int(p[0]), int(p[1])) for p in pairs]
@@ -77,6 +83,8 @@ class Problem:
     def _check_images(self, t: torch.Tensor, pairs=None):
         if not t.is_cuda or not t.is_contiguous():
             raise ValueError("image buffers must be contiguous CUDA tensors")
+        if t.device != self.device:
+            raise ValueError(f"image buffer on {t.device}, the problem lives on {self.device}")
         if t.dtype != self.dtype:
             raise ValueError(f"expected {self.dtype}, got {t.dtype}")
         if t.numel() != self.n_pixels(pairs):
@@ -85,6 +93,8 @@ class Problem:
     def _check_theta(self, theta: torch.Tensor):
         if not theta.is_cuda or theta.dtype != torch.float64 or theta.numel() != self.p or not theta.is_contiguous():
             raise ValueError(f"theta must be a contiguous float64 CUDA tensor of {self.p} values")
+        if theta.device != self.device:
+            raise ValueError(f"theta on {theta.device}, the problem lives on {self.device}")
 
     def empty(self, pairs=None) -> torch.Tensor:
         return torch.empty(self.n_pixels(pairs), dtype=self.dtype, device=self.device)
@@ -181,7 +191,10 @@ class Problem:
                          1 if warm_start else 0, 1 if graph else 0)
         sc = None
         if nsc_scale is not None:
-            sc = (C.c_double * n)(*[float(v) for v in nsc_scale])
+            vals = [float(v) for v in nsc_scale]
+            if len(vals) != n:
+                raise ValueError(f"nsc_scale needs one value per solved pair ({n}), got {len(vals)}")
+            sc = (C.c_double * n)(*vals)
         info = (L.SolveInfo * n)()
         allow = (L.BL_OK, L.BL_ENOCONV) if allow_noconv else (L.BL_OK,)
         L.check(self.lib.bl_hessian_solve(self.h, pa, n, C.byref(o), _ptr(g), _ptr(w), sc, info),
