@@ -6,10 +6,11 @@
  * "Efficient gradient-based methods for bilevel learning via recycling
  * Krylov subspaces"):
  *
- *   bl_problem_create   pairs (y_k, x*_k), blur A_k, regulariser R(x, theta)
+ *   bl_problem_create   pairs (y_k, x*_k), operator A_k (blur or inpainting mask), regulariser R(x, theta)
  *   bl_lower_solve      x^_k = argmin_x Phi_k(x, theta)          (eq. (1.1), (5.1); L-BFGS, Section 5.1)
- *   bl_ritz_update      refresh U, C = H U from W = [U, V]       (Section 3, eq. (3.3) outer form)
- *   bl_hessian_solve    H_k w_k = grad ell_k by recycled CG     (Section 2.2, eq. (2.5), Section 4 stopping)
+ *   bl_ritz_update      refresh U, C = H U from W = [U, V]       (Section 3, eq. (3.3) outer / (3.4) inner form)
+ *   bl_hessian_solve    H_k w_k = grad ell_k by recycled CG or recycled MINRES
+ *                       (Section 2.2, eq. (2.5), Algorithm 3, Section 4 stopping)
  *   bl_hypergrad        g_k = J_k w_k = -(D^2_{theta x} Phi_k)^T w_k   (eq. (2.7))
  *
  * Conventions shared by every entry point
@@ -19,8 +20,10 @@
  *     double for BL_FP64.
  *   - A "packed" buffer holds the images of the listed pairs back to back, in the
  *     order of the `pairs` index array, each H_k * W_k elements.
- *   - Device pointers are CUDA device memory owned by the caller unless stated;
- *     the library reads them during the call's stream work and keeps no reference.
+ *   - Device pointers are CUDA device memory owned by the caller unless stated, on the
+ *     device that was current when the problem was created (the library cannot check this:
+ *     memory of another device, or host memory, is undefined behaviour on the GPU); the
+ *     library reads them during the call's stream work and keeps no reference.
  *   - theta (length p, double, device) is laid out per filter as
  *     [alpha_1, taps_1 (f*f row-major, tap (a, b) at (a + r) * f + (b + r)), alpha_2, ...]
  *     for the Fields-of-Experts regulariser (Section 5), p = N (f*f + 1); p = 1 for TV.
@@ -169,7 +172,11 @@ typedef struct bl_problem bl_problem;
 bl_status bl_problem_create(const bl_pair_desc* pairs, int32_t K, const bl_reg_desc* reg,
                             const void* y_packed, const void* xstar_packed, void* cuda_stream,
                             bl_problem** out);
+/* Synchronises the problem's stream, destroys its CUDA graphs and frees all device memory the
+ * problem owns; prob may be NULL.  Caller buffers are untouched. */
 void bl_problem_destroy(bl_problem* prob);
+/* Make cuda_stream (a cudaStream_t, NULL = legacy default stream) the stream of all later calls.
+ * The caller orders it after the old stream's pending work; captured CUDA graphs are kept. */
 bl_status bl_set_stream(bl_problem* prob, void* cuda_stream);
 
 /* Number of hyperparameters p and total pixels of the listed pairs (host values). */
@@ -181,7 +188,8 @@ int64_t bl_num_pixels(const bl_problem* prob, const int32_t* pairs, int32_t npai
 bl_status bl_set_data(bl_problem* prob, const int32_t* pairs, int32_t npairs, const void* y_packed,
                       const void* xstar_packed);
 
-/* y_k = A_k x_k for each listed pair (the blur of Section 5.2); x, out packed, device. */
+/* y_k = A_k x_k for each listed pair (the blur of Section 5.2, or the inpainting mask of
+ * Section 5.1 for pairs created with one); x, out packed, device. */
 bl_status bl_forward(bl_problem* prob, const int32_t* pairs, int32_t npairs, const void* x_packed,
                      void* out_packed);
 
@@ -207,15 +215,18 @@ bl_status bl_gradient(bl_problem* prob, const int32_t* pairs, int32_t npairs, co
 bl_status bl_hvp(bl_problem* prob, const int32_t* pairs, int32_t npairs, const void* v_packed,
                  void* out_packed);
 
-/* Refresh the recycle space of each listed pair (Section 3, outer form eq. (3.3)):
- * W = [U^(i-1), V^(i-1)] is orthonormalised, projected with the current H (and J for RGSV),
+/* Refresh the recycle space of each listed pair (Section 3; opts->variant picks the outer form of
+ * eq. (3.3), or the inner form of eq. (3.4), which projects with the Hessian of the last CG solve
+ * rebuilt from its Lanczos record):
+ * W = [U^(i-1), V^(i-1)] is orthonormalised, projected with H (and J for RGSV),
  * the s selected vectors U~ are QR-normalised so that C = H U, C^T C = I (Section 2.2.2), and
  * for RGSV the estimate operator Z = W~ V~_H diag(mu) of eq. (4.2) is stored.
  * A pair without a stored basis keeps an empty recycle space. */
 bl_status bl_ritz_update(bl_problem* prob, const int32_t* pairs, int32_t npairs,
                          const bl_recycle_opts* opts);
 
-/* Solve H_k w_k = g_k for the listed pairs in one batched recycled-CG run (Section 2.2):
+/* Solve H_k w_k = g_k for the listed pairs in one batched run of (recycled) CG or (recycled)
+ * MINRES, as opts->method says (Section 2.2, Algorithm 3):
  *   g_packed: device right-hand sides, or NULL for g_k = x^_k - x*_k (grad of 1/2||x - x*||^2);
  *   w_packed: device, in = warm start (if opts->warm_start), out = solution;
  *   nsc_scale: host, npairs doubles used by a relative NSC rule, or NULL;
