@@ -10,8 +10,12 @@ relative error of a tight reference solve (checked after the timed region and re
 
 Arms
   default            the CUDA path (libbl), recycled CG with the chosen strategy; the same run
-                     also times plain warm-started CG on the same sequence.
+                     also times plain CG on the same sequence, warm-started and cold-started.
   --impl reference   the FP64 CPU checker on a bounded sample of the workload (host cores).
+
+Other workloads: --workload inpaint (1024 pairs of 28 x 28, Section 5.1's shape) and
+--workload deconv --method minres (512 pairs of 64 x 64, phi = log(1 + s^2), Section 5.2's
+shape); --rtol sets the residual tolerance, --no-graph runs both loops host-polled (profilers).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Under torchrun (N > 1) every rank solves its own batch (weak scaling) and the mean
