@@ -135,12 +135,18 @@ def test_minres_is_krylov_least_squares(k, rng):
     np.testing.assert_allclose(out["r"], g - H @ out["w"], atol=1e-8)
 
 
+@pytest.mark.parametrize("indefinite", [False, True])
 @pytest.mark.parametrize("k", [1, 3, 6])
-def test_rminres_solves_coupled_least_squares(k, rng):
+def test_rminres_solves_coupled_least_squares(k, indefinite, rng):
     """RMINRES minimises ||r0 - H [V_k U] [y; z]|| (eq. (2.11)) over the augmented
-    Krylov space of (I - C C^T) H, after the initial projection onto C."""
+    Krylov space of (I - C C^T) H, after the initial projection onto C; also for a symmetric
+    indefinite H (the non-convex phi of Section 5.2), where C = H U, C^T C = I still holds."""
     n, s = 24, 3
     H = spd(rng, n, 30)
+    if indefinite:
+        Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+        lam = np.concatenate([-np.logspace(0, 1, 5), np.logspace(0, 1.5, n - 5)])
+        H = (Q * lam) @ Q.T
     g = rng.standard_normal(n)
     w0 = rng.standard_normal(n)
     U, C = make_recycle(rng, H, s)
