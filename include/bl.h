@@ -221,7 +221,10 @@ bl_status bl_hvp(bl_problem* prob, const int32_t* pairs, int32_t npairs, const v
  * W = [U^(i-1), V^(i-1)] is orthonormalised, projected with H (and J for RGSV),
  * the s selected vectors U~ are QR-normalised so that C = H U, C^T C = I (Section 2.2.2), and
  * for RGSV the estimate operator Z = W~ V~_H diag(mu) of eq. (4.2) is stored.
- * A pair without a stored basis keeps an empty recycle space. */
+ * A pair without a stored basis keeps an empty recycle space.  A pair whose projected matrix is not
+ * positive definite (T for RGSV, C~^T C~ in the CholeskyQR of C~ = H U~) is left with an empty
+ * recycle space (its next solve is plain CG) while the other pairs are refreshed; the call then
+ * returns BL_EBREAKDOWN. */
 bl_status bl_ritz_update(bl_problem* prob, const int32_t* pairs, int32_t npairs,
                          const bl_recycle_opts* opts);
 

@@ -154,17 +154,25 @@ class Problem:
         L.check(self.lib.bl_hvp(self.h, pa, n, _ptr(v), _ptr(out)), "bl_hvp")
         return out
 
-    def ritz_update(self, strategy, s: int, pairs=None, variant: str = "outer"):
+    def ritz_update(self, strategy, s: int, pairs=None, variant: str = "outer", allow_breakdown: bool = True):
         """variant "outer": project W with the current Hessian (eq. (3.3)); "inner": with the Hessian
         of the last solve, rebuilt from its Lanczos record (eq. (3.4); that solve must have used
-        store_basis="lanczos")."""
+        store_basis="lanczos").
+
+        A pair whose projected matrix is not positive definite (RGSV needs T^{-1}; CholeskyQR of
+        C = H U needs a full-rank U) gets an empty recycle space, so its next solve is plain CG,
+        while the other pairs are refreshed; the library reports this as BL_EBREAKDOWN.  With
+        allow_breakdown (the default) that status is not raised: the return value is False when
+        some pair was left without a recycle space, True otherwise."""
         st = parse(strategy) if isinstance(strategy, str) else strategy
         if not st.recycles:
-            return
+            return True
         pa, n, _ = self._pairs(pairs)
         o = L.RecycleOpts(L.BL_RECYCLE[st.kind], L.BL_SIZE[st.size], L.BL_SIDE[st.side], int(s),
                           L.BL_REFRESH[variant])
-        L.check(self.lib.bl_ritz_update(self.h, pa, n, C.byref(o)), "bl_ritz_update")
+        allow = (L.BL_OK, L.BL_EBREAKDOWN) if allow_breakdown else (L.BL_OK,)
+        status = L.check(self.lib.bl_ritz_update(self.h, pa, n, C.byref(o)), "bl_ritz_update", allow)
+        return status == L.BL_OK
 
     def hessian_solve(self, w: torch.Tensor, g: Optional[torch.Tensor] = None, pairs=None, recycle: bool = True,
                       nsc: bool = False, tol: float = 1e-4, relative: bool = True, maxit: int = 2000,
