@@ -171,8 +171,10 @@ struct bl_problem {
   unsigned char* d_opmask = nullptr;   // inpainting masks of all pairs (n_tot bytes), if any pair has one
   // Lanczos-relation record of the last CG solve (BL_STORE_LANCZOS): per pair and step j < KMAX,
   // alpha_j, rho_j = ||r_j||^2 and C^T H p_j; lz_k[k] = 1 when pair k's stored basis is such a record
+  // (a refresh or a checkpoint import consumes it); lz_u[k] = 1 when that solve deflated with the
+  // recycle space the pair holds now, so its C^T H p_j complete the relation for [U, V]
   double *lz_alpha = nullptr, *lz_rho = nullptr, *lz_c = nullptr;
-  std::vector<int> lz_k;
+  std::vector<int> lz_k, lz_u;
   void *U = nullptr, *C = nullptr, *Z = nullptr, *V = nullptr;
   void *W = nullptr, *Wt = nullptr, *HWt = nullptr;
   bl::SolveState* st = nullptr;
@@ -197,7 +199,7 @@ struct bl_problem {
 
   // dense small-matrix workspace (FP64)
   double *dG = nullptr, *dT = nullptr, *dJ = nullptr, *dY = nullptr, *dY2 = nullptr, *dY3 = nullptr;
-  int* d_tk = nullptr;      // reduced basis size per pair
+  int* d_tk = nullptr;      // 3K ints: reduced basis size t' per pair, selected s, previous s in W
 
   // L-BFGS
   void *lx = nullptr, *lg = nullptr, *ld = nullptr, *lxt = nullptr, *lgt = nullptr, *lq = nullptr;

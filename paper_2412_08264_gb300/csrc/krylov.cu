@@ -975,6 +975,7 @@ static bl_status solve_impl(bl_problem* P, const int* mask_host, const bl_krylov
       P->kb_k[k] = a.lanczos ? std::min(S.iters, P->KMAX - 1) : std::min(S.iters, P->KMAX);
       P->head_k[k] = S.iters;
       P->lz_k[k] = a.lanczos;
+      P->lz_u[k] = s_eff[k] == P->s_k[k] ? 1 : 0;
     }
   }
   return BL_OK;

@@ -301,6 +301,7 @@ bl_status bl_problem_create(const bl_pair_desc* pairs, int32_t K, const bl_reg_d
   P->hz_k.assign(K, 0);
   P->head_k.assign(K, 0);
   P->lz_k.assign(K, 0);
+  P->lz_u.assign(K, 0);
 
   bl_status st = BL_OK;
 #define BL_ALLOC(expr)              \
@@ -362,7 +363,7 @@ bl_status bl_problem_create(const bl_pair_desc* pairs, int32_t K, const bl_reg_d
   BL_ALLOC(dalloc((void**)&P->d_hasz, K * sizeof(int)));
   BL_ALLOC(dalloc((void**)&P->d_active, 3 * K * sizeof(int)));
   BL_ALLOC(dalloc((void**)&P->d_cols, 2 * K * sizeof(int)));
-  BL_ALLOC(dalloc((void**)&P->d_tk, 2 * K * sizeof(int)));
+  BL_ALLOC(dalloc((void**)&P->d_tk, 3 * K * sizeof(int)));
   BL_ALLOC(dalloc((void**)&P->d_flag, sizeof(int)));
   BL_ALLOC(dalloc((void**)&P->d_zero, K * sizeof(int)));
   BL_ALLOC(dalloc((void**)&P->d_loop, 2 * sizeof(int)));
@@ -680,6 +681,7 @@ bl_status bl_recycle_import(bl_problem* P, int32_t pair, const void* buf, size_t
   P->s_k[pair] = s;
   P->hz_k[pair] = hd.hasz;
   P->kb_k[pair] = 0;
+  P->lz_k[pair] = 0;
   BL_CUDA_TRY(cudaMemcpyAsync(P->d_s, P->s_k.data(), P->K * sizeof(int), cudaMemcpyHostToDevice, P->stream));
   BL_CUDA_TRY(cudaMemcpyAsync(P->d_hasz, P->hz_k.data(), P->K * sizeof(int), cudaMemcpyHostToDevice, P->stream));
   BL_CUDA_TRY(cudaStreamSynchronize(P->stream));

@@ -495,21 +495,27 @@ __global__ void k_lanczos_rel(const int* mask, const int* s_old, const int* tcol
 template <typename T>
 static bl_status refresh_impl(bl_problem* P, const std::vector<int>& mask_host, const bl_recycle_opts* o) {
   const int K = P->K, TM = P->TM;
-  std::vector<int> msk(K, 0), tcols(K, 0);
+  const bool inner = o->variant == BL_REFRESH_INNER;
+  // sprev: columns of the previous U in W = [U, V].  The inner form takes U only when the recorded
+  // solve deflated with it (its C^T H p_j then complete the relation); after a solve without that
+  // space, W is the Krylov basis alone, whose plain Lanczos relation is exact
+  std::vector<int> msk(K, 0), tcols(K, 0), sprev(K, 0);
   bool any = false;
   for (int k = 0; k < K; ++k) {
     if (!mask_host[k]) continue;
-    const int t = P->s_k[k] + P->kb_k[k];
-    if (t == 0) continue;            // no basis yet: the recycle space stays empty
+    sprev[k] = (!inner || P->lz_u[k]) ? P->s_k[k] : 0;
+    const int t = sprev[k] + P->kb_k[k];
+    // no basis yet: the recycle space stays empty (an inner refresh of a pair that holds a space
+    // but has no record to relate it to is refused below)
+    if (t == 0 && !(inner && P->s_k[k])) continue;
     msk[k] = 1;
     tcols[k] = t;
     any = true;
   }
   if (!any) return BL_OK;
-  const bool inner = o->variant == BL_REFRESH_INNER;
   if (inner)
     for (int k = 0; k < K; ++k)
-      if (msk[k] && !P->lz_k[k])
+      if (msk[k] && (!P->lz_k[k] || tcols[k] == 0))
         return fail(BL_ESTATE, "inner refresh needs the last solve's Lanczos record (BL_STORE_LANCZOS)");
   int* d_mask = P->d_active + 2 * K;      // refresh mask
   int* d_t = P->d_cols;                   // t per pair
@@ -522,11 +528,11 @@ static bl_status refresh_impl(bl_problem* P, const std::vector<int>& mask_host, 
     if (!msk[k]) continue;
     const auto& ph = P->ph[k];
     char* Wk = (char*)P->W + ph.off * TM * P->esz;
-    if (P->s_k[k])
-      BL_CUDA_TRY(cudaMemcpyAsync(Wk, (const char*)P->U + ph.off * P->SMAX * P->esz, (size_t)P->s_k[k] * ph.n * P->esz,
+    if (sprev[k])
+      BL_CUDA_TRY(cudaMemcpyAsync(Wk, (const char*)P->U + ph.off * P->SMAX * P->esz, (size_t)sprev[k] * ph.n * P->esz,
                                   cudaMemcpyDeviceToDevice, P->stream));
     if (P->kb_k[k])
-      BL_CUDA_TRY(cudaMemcpyAsync(Wk + (size_t)P->s_k[k] * ph.n * P->esz, (const char*)P->V + ph.off * P->KMAX * P->esz,
+      BL_CUDA_TRY(cudaMemcpyAsync(Wk + (size_t)sprev[k] * ph.n * P->esz, (const char*)P->V + ph.off * P->KMAX * P->esz,
                                   (size_t)P->kb_k[k] * ph.n * P->esz, cudaMemcpyDeviceToDevice, P->stream));
   }
   int tmax = 0;
@@ -540,16 +546,18 @@ static bl_status refresh_impl(bl_problem* P, const std::vector<int>& mask_host, 
       const auto& ph = P->ph[k];
       char* Xk = (char*)P->Wt + ph.off * TM * P->esz;
       xc[k] = tcols[k] + 1;
-      if (P->s_k[k])
+      if (sprev[k])
         BL_CUDA_TRY(cudaMemcpyAsync(Xk, (const char*)P->C + ph.off * P->SMAX * P->esz,
-                                    (size_t)P->s_k[k] * ph.n * P->esz, cudaMemcpyDeviceToDevice, P->stream));
-      BL_CUDA_TRY(cudaMemcpyAsync(Xk + (size_t)P->s_k[k] * ph.n * P->esz, (const char*)P->V + ph.off * P->KMAX * P->esz,
+                                    (size_t)sprev[k] * ph.n * P->esz, cudaMemcpyDeviceToDevice, P->stream));
+      BL_CUDA_TRY(cudaMemcpyAsync(Xk + (size_t)sprev[k] * ph.n * P->esz, (const char*)P->V + ph.off * P->KMAX * P->esz,
                                   (size_t)(P->kb_k[k] + 1) * ph.n * P->esz, cudaMemcpyDeviceToDevice, P->stream));
     }
     BL_CUDA_TRY(cudaMemcpyAsync(d_tk, xc.data(), K * sizeof(int), cudaMemcpyHostToDevice, P->stream));
+    int* d_sprev = P->d_tk + 2 * K;
+    BL_CUDA_TRY(cudaMemcpyAsync(d_sprev, sprev.data(), K * sizeof(int), cudaMemcpyHostToDevice, P->stream));
     {
       ProfScope ps(P, BL_KC_DENSE);
-      k_lanczos_rel<<<K, 256, 0, P->stream>>>(d_mask, P->d_s, d_t, P->lz_alpha, P->lz_rho, P->lz_c, P->KMAX, P->SMAX,
+      k_lanczos_rel<<<K, 256, 0, P->stream>>>(d_mask, d_sprev, d_t, P->lz_alpha, P->lz_rho, P->lz_c, P->KMAX, P->SMAX,
                                               TM, P->dY2);
       BL_LAUNCH_CHECK(P);
     }
@@ -668,7 +676,8 @@ static bl_status refresh_impl(bl_problem* P, const std::vector<int>& mask_host, 
       P->s_k[k] = sn[k];
       P->hz_k[k] = (o->kind == BL_RECYCLE_RGSV && sn[k] > 0) ? 1 : 0;
     }
-    P->kb_k[k] = 0;   // the basis has been consumed
+    P->kb_k[k] = 0;   // the basis and its Lanczos record have been consumed
+    P->lz_k[k] = 0;
   }
   BL_CUDA_TRY(cudaMemcpyAsync(P->d_s, P->s_k.data(), K * sizeof(int), cudaMemcpyHostToDevice, P->stream));
   BL_CUDA_TRY(cudaMemcpyAsync(P->d_hasz, P->hz_k.data(), K * sizeof(int), cudaMemcpyHostToDevice, P->stream));
