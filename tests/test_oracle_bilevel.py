@@ -110,3 +110,64 @@ def test_adam_closed_form_first_step():
     th = np.array([1.0, -2.0, 0.5])
     g = np.array([3.0, -0.1, 2e-3])
     np.testing.assert_allclose(opt.step(th, g), th - 1e-2 * np.sign(g), rtol=1e-12)
+
+
+class _ScalarBilevel:
+    """A one-parameter bilevel problem with closed forms, for listing Algorithm 1 by hand.
+
+    Lower level Phi(x, theta) = 1/2 (x - theta)^2, so x^(theta) = theta, H = 1 and
+    D^2_{theta x} Phi = -1; upper loss L = 1/2 a (x^ - c)^2.  Then grad ell = a (x^ - c),
+    w = grad ell and the hypergradient (eq. (2.7)) is -(-1) w = a (theta - c).  Every lower
+    solve is recorded, so the test sees each Armijo trial point."""
+
+    K = 1
+
+    def __init__(self, a, c):
+        self.a, self.c = a, c
+        self.trials = []
+
+    def solve_lower(self, theta, x0s=None, gtol=1e-8):
+        th = float(np.asarray(theta).ravel()[0])
+        self.trials.append(th)
+        return [np.array([th])], [{}]
+
+    def loss(self, xhats):
+        return 0.5 * self.a * float((xhats[0][0] - self.c) ** 2)
+
+    def rhs(self, k, xhat):
+        return self.a * (xhat - self.c)
+
+    def hypergradient(self, theta, xhats, ws):
+        return np.mean([w for w in ws], axis=0)
+
+
+def _identity_solve(k, xhat, theta, g):
+    return np.array(g, dtype=np.float64)
+
+
+@pytest.mark.parametrize("eta, trials, steps, accepted", [
+    # L = 0.75 theta^2, theta0 = 1, beta0 = 1, rho = 1/2, eta = 1e-4:
+    #   step 1: d = 1.5;  trial beta rho^0 = 1 -> theta = -0.5, L = 0.1875 < 0.75 - 2.25e-4: accept; beta = 2
+    #   step 2: d = -0.75; trial 2 -> theta = 1.0 (L = 0.75, reject); trial 1 -> theta = 0.25 (accept); beta = 2
+    #   step 3: d = 0.375; trial 2 -> theta = -0.5 (reject); trial 1 -> theta = -0.125 (accept)
+    (1e-4, [1.0, -0.5, 1.0, 0.25, -0.5, -0.125], [1.0, 1.0, 1.0], [1.0, -0.5, 0.25, -0.125]),
+    # the same problem with eta = 0.6, where the sufficient-decrease term decides:
+    #   step 1: trial 1 -> -0.5: 0.1875 < 0.75 - 0.6 * 2.25 fails; trial 0.5 -> 0.25: 0.046875 < 0.075: accept; beta = 1
+    #   step 2: d = 0.375; trial 1 -> -0.125: 0.01172 < -0.0375 fails; trial 0.5 -> 0.0625: 0.00293 < 0.00469: accept
+    #   step 3: d = 0.09375; trial 1 -> -0.03125 fails; trial 0.5 -> 0.015625: 1.83e-4 < 2.93e-4: accept
+    (0.6, [1.0, -0.5, 0.25, -0.125, 0.0625, -0.03125, 0.015625], [0.5, 0.5, 0.5], [1.0, 0.25, 0.0625, 0.015625]),
+])
+def test_gradient_descent_lists_every_armijo_trial(eta, trials, steps, accepted):
+    """Algorithms 1-2 on a worked case: the trial points beta rho^{j-1}, the sufficient-decrease test
+    L(theta_j) < L(theta) - eta beta rho^{j-1} ||d||^2 and the next initial step 2 beta rho^{j-1} are
+    fixed by the listing above (a dropped doubling, rho^j for rho^{j-1}, a flipped step sign or
+    ||d|| for ||d||^2 each change the list)."""
+    prob = _ScalarBilevel(a=1.5, c=0.0)
+    log = []
+    theta, xhats, thetas = gradient_descent(prob, np.array([1.0]), 3, _identity_solve, beta0=1.0, rho=0.5,
+                                            eta=eta, log=log)
+    np.testing.assert_allclose(prob.trials, trials, rtol=0, atol=1e-15)
+    np.testing.assert_allclose([e["step_len"] for e in log], steps, rtol=0, atol=0)
+    np.testing.assert_allclose([float(t[0]) for t in thetas], accepted, rtol=0, atol=1e-15)
+    np.testing.assert_allclose([e["loss"] for e in log], [0.75 * t ** 2 for t in accepted[1:]], rtol=1e-15)
+    assert float(theta[0]) == accepted[-1] and float(xhats[0][0]) == accepted[-1]
