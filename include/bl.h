@@ -304,8 +304,9 @@ const char* bl_last_error(void);
  * make that first call before any stream capture.  Every call uses the same array and rewrites
  * what it reads, so results never depend on an earlier call, but calls whose GPU work overlaps
  * (unordered streams) race on it: order them on one stream.  No cudaMalloc, cudaFree or
- * allocating library routine is called.  Returns BL_EINVAL on invalid sizes or options, BL_ECUDA
- * if a launch fails. */
+ * allocating library routine is called.  Every argument is validated before the first CUDA call.
+ * Returns BL_EINVAL on invalid sizes or options; BL_ECUDA if a launch fails, or if a CUDA error left
+ * by earlier work on the calling thread was pending on entry (reported, not cleared; nothing runs). */
 bl_status bl_jw_fp32_static(const float* xhat, const float* w, int32_t height, int32_t width,
                             const double* theta, int32_t n_filters, int32_t filter_size, int32_t phi,
                             double phi_eps, double* out, void* cuda_stream);

@@ -149,19 +149,31 @@ extern "C" bl_status bl_jw_fp32_static(const float* xhat, const float* w, int32_
   if ((unsigned long long)n_tiles * (unsigned long long)p > kPartials)
     return bl::fail(BL_EINVAL, "image too large for the static scratch: ceil(H/32) * ceil(W/32) * p must be <= " +
                                    std::to_string(kPartials) + ", got " + std::to_string(n_tiles * p));
+  // An error left on this thread by earlier, unrelated work would otherwise surface as this call's
+  // launch failure (and be cleared by the check): report it untouched instead.
+  const cudaError_t pending = cudaPeekAtLastError();
+  if (pending != cudaSuccess)
+    return bl::fail(BL_ECUDA, std::string("a CUDA error was pending before this call (left untouched): ") +
+                                  cudaGetErrorString(pending));
   double* s = nullptr;
   bl_status st = scratch_address(&s);
   if (st != BL_OK) return st;
   cudaStream_t stream = (cudaStream_t)cuda_stream;
+  auto launched = [](const char* what) -> bl_status {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return bl::fail(BL_ECUDA, std::string(what) + " launch: " + cudaGetErrorString(e));
+    return BL_OK;
+  };
   k_static_theta<<<(p + 255) / 256, 256, 0, stream>>>(theta, n_filters, FF, s);
+  if ((st = launched("k_static_theta")) != BL_OK) return st;
   switch (filter_size) {
     case 1: k_static_jw<1><<<(unsigned)n_tiles, 256, 0, stream>>>(xhat, w, height, width, n_filters, (float)phi_eps, phi, p, s); break;
     case 3: k_static_jw<3><<<(unsigned)n_tiles, 256, 0, stream>>>(xhat, w, height, width, n_filters, (float)phi_eps, phi, p, s); break;
     case 5: k_static_jw<5><<<(unsigned)n_tiles, 256, 0, stream>>>(xhat, w, height, width, n_filters, (float)phi_eps, phi, p, s); break;
     default: k_static_jw<7><<<(unsigned)n_tiles, 256, 0, stream>>>(xhat, w, height, width, n_filters, (float)phi_eps, phi, p, s); break;
   }
+  if ((st = launched("k_static_jw")) != BL_OK) return st;
   k_static_reduce<<<(p + 255) / 256, 256, 0, stream>>>(s, (int)n_tiles, p, out);
-  const cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return bl::fail(BL_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e));
+  if ((st = launched("k_static_reduce")) != BL_OK) return st;
   return BL_OK;
 }

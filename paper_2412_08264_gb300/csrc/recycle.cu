@@ -500,11 +500,21 @@ static bl_status refresh_impl(bl_problem* P, const std::vector<int>& mask_host, 
   // solve deflated with it (its C^T H p_j then complete the relation); after a solve without that
   // space, W is the Krylov basis alone, whose plain Lanczos relation is exact
   std::vector<int> msk(K, 0), tcols(K, 0), sprev(K, 0);
-  bool any = false;
+  bool any = false, cleared = false;
   for (int k = 0; k < K; ++k) {
     if (!mask_host[k]) continue;
     sprev[k] = (!inner || P->lz_u[k]) ? P->s_k[k] : 0;
     const int t = sprev[k] + P->kb_k[k];
+    if (inner && t == 0 && P->s_k[k] && P->lz_k[k]) {
+      // the recorded solve neither deflated with this pair's space nor took a step (a warm start
+      // already below tolerance): nothing relates the space to the new Hessian, so this pair alone
+      // loses it (its next solve is plain CG) and the record is consumed; reported as a breakdown
+      P->s_k[k] = 0;
+      P->hz_k[k] = 0;
+      P->lz_k[k] = 0;
+      cleared = true;
+      continue;
+    }
     // no basis yet: the recycle space stays empty (an inner refresh of a pair that holds a space
     // but has no record to relate it to is refused below)
     if (t == 0 && !(inner && P->s_k[k])) continue;
@@ -512,7 +522,14 @@ static bl_status refresh_impl(bl_problem* P, const std::vector<int>& mask_host, 
     tcols[k] = t;
     any = true;
   }
-  if (!any) return BL_OK;
+  if (!any) {
+    if (!cleared) return BL_OK;
+    BL_CUDA_TRY(cudaMemcpyAsync(P->d_s, P->s_k.data(), K * sizeof(int), cudaMemcpyHostToDevice, P->stream));
+    BL_CUDA_TRY(cudaMemcpyAsync(P->d_hasz, P->hz_k.data(), K * sizeof(int), cudaMemcpyHostToDevice, P->stream));
+    BL_CUDA_TRY(cudaStreamSynchronize(P->stream));   // the host vectors are rewritten by later calls
+    return fail(BL_EBREAKDOWN, "inner recycle refresh: a pair whose recorded solve took no step without its "
+                               "recycle space was left with an empty space");
+  }
   if (inner)
     for (int k = 0; k < K; ++k)
       if (msk[k] && (!P->lz_k[k] || tcols[k] == 0))
@@ -682,6 +699,11 @@ static bl_status refresh_impl(bl_problem* P, const std::vector<int>& mask_host, 
   BL_CUDA_TRY(cudaMemcpyAsync(P->d_s, P->s_k.data(), K * sizeof(int), cudaMemcpyHostToDevice, P->stream));
   BL_CUDA_TRY(cudaMemcpyAsync(P->d_hasz, P->hz_k.data(), K * sizeof(int), cudaMemcpyHostToDevice, P->stream));
   if (broke) return fail(BL_EBREAKDOWN, "recycle refresh: projected Hessian not positive definite");
+  if (cleared) {
+    BL_CUDA_TRY(cudaStreamSynchronize(P->stream));
+    return fail(BL_EBREAKDOWN, "inner recycle refresh: a pair whose recorded solve took no step without its "
+                               "recycle space was left with an empty space");
+  }
   return BL_OK;
 }
 

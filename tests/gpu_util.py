@@ -50,3 +50,11 @@ def rel(a, b):
     a = np.asarray(a, dtype=np.float64).ravel()
     b = np.asarray(b, dtype=np.float64).ravel()
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def max_elem(a, b):
+    """Largest element-wise deviation relative to the largest reference magnitude: a bar on every
+    element (tile seams, image borders), which a norm ratio over many elements can dilute."""
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))

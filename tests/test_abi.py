@@ -118,3 +118,39 @@ def test_strategy_grammar_rejects(bad):
     from paper_2412_08264_gb300.strategy import parse
     with pytest.raises(ValueError):
         parse(bad)
+
+
+def test_static_jw_validates_before_any_cuda_call(tmp_path):
+    """bl_jw_fp32_static rejects sizes beyond its fixed scratch and invalid options before it makes a
+    CUDA call: run in a child process that sees no GPU, with placeholder pointers that are never
+    dereferenced (a regression that reached a launch would fail there with BL_ECUDA, not touch a GPU)."""
+    import subprocess
+    import sys
+    script = r'''
+import ctypes, sys
+sys.path.insert(0, %r)
+from paper_2412_08264_gb300 import _lib as L
+lib = L.load()
+d = ctypes.c_void_p(256)
+cases = [
+    # 2048 x 2048 with 48 7x7 filters: 64 * 64 tiles * 2400 values > 524288
+    ((d, d, 2048, 2048, d, 48, 7, 0, 0.01, d, None), b"static scratch"),
+    ((d, d, 64, 64, d, 4, 4, 0, 0.01, d, None), b"filter_size"),
+    ((d, d, 0, 64, d, 4, 5, 0, 0.01, d, None), b"sizes"),
+    ((d, d, 64, 64, d, 65, 5, 0, 0.01, d, None), b"n_filters"),
+    ((d, d, 64, 64, d, 4, 5, 7, 0.01, d, None), b"phi"),
+    ((d, d, 64, 64, d, 4, 5, 0, 0.0, d, None), b"phi_eps"),
+    ((None, d, 64, 64, d, 4, 5, 0, 0.01, d, None), b"null"),
+]
+for args, word in cases:
+    st = lib.bl_jw_fp32_static(*args)
+    msg = lib.bl_last_error()
+    assert st == L.BL_EINVAL, (args, st, msg)
+    assert word in msg, (word, msg)
+print("ok")
+''' % ROOT
+    env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
+    from paper_2412_08264_gb300 import build
+    build.build()
+    r = subprocess.run([sys.executable, "-c", script], capture_output=True, text=True, env=env, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", r.stdout + r.stderr

@@ -113,3 +113,56 @@ def test_inner_refresh_needs_a_lanczos_record():
         P.ritz_update("Ritz-S", 4, variant="inner")
     with pytest.raises(Exception, match="MINRES keeps"):
         P.hessian_solve(w, recycle=False, tol=1e-4, store_basis="lanczos", method="minres")
+
+
+def test_inner_refresh_leaves_only_a_zero_step_pair_without_space():
+    """A pair whose recorded solve ran without its recycle space and took no step (warm start already
+    at the solution) has nothing relating its space to the new Hessian: the inner refresh clears
+    that pair alone (BL_EBREAKDOWN, reported by the binding as False) and refreshes the others as
+    the checker does."""
+    wl = synth.uneven_foe([(40, 44), (36, 30)], n_filters=3, f=5, blur_radius=2, seed=9)
+    kmax, s = 40, 4
+    P, prob, dt = make(wl, "fp64", max_recycle=s, max_basis=kmax)
+    rng = np.random.default_rng(9)
+    th = wl.theta0.copy()
+    ths = [th, th - 0.005 * rng.standard_normal(th.shape)]
+    ths.append(ths[1] - 0.005 * rng.standard_normal(th.shape))
+    pts = [prob.solve_lower(t, gtol=1e-9)[0] for t in ths]
+    # step 0: plain solves with the Lanczos record; refresh at the next point gives both pairs a space
+    P.set_point(torch.tensor(ths[0], dtype=torch.float64, device=DEV), packed(pts[0], dt))
+    w = P.zeros()
+    P.hessian_solve(w, recycle=True, tol=1e-7, relative=True, warm_start=False, maxit=2000, store_basis="lanczos")
+    P.set_point(torch.tensor(ths[1], dtype=torch.float64, device=DEV), packed(pts[1], dt))
+    assert P.ritz_update("Ritz-S", s, variant="inner")
+    assert P.recycle_dim(0) == s and P.recycle_dim(1) == s
+    # step 1: pair 0 starts at its exact solution (no step), pair 1 from zero; no recycling
+    x1 = pts[1]
+    wstar0 = prob.reference_w(0, x1[0], ths[1])
+    w = packed([wstar0.reshape(x1[0].shape), np.zeros(x1[1].shape)], dt)
+    info = P.hessian_solve(w, recycle=False, tol=1e-7, relative=True, warm_start=True, maxit=2000,
+                           store_basis="lanczos")
+    assert info[0]["iters"] == 0 and info[1]["iters"] > 0
+    AH1 = prob.apply_H(1, x1[1], ths[1])
+    g1 = prob.rhs(1, x1[1])
+    out = rcg(AH1, g1, np.zeros_like(g1), None, None, tol=1e-7 * np.linalg.norm(g1), maxit=2000)
+    assert abs(info[1]["iters"] - out["iters"]) <= 1
+    m = min(info[1]["iters"], kmax - 1)
+    V1 = out["V"][:, :m]
+    # step 2: inner refresh
+    x2 = pts[2]
+    P.set_point(torch.tensor(ths[2], dtype=torch.float64, device=DEV), packed(x2, dt))
+    assert P.ritz_update("Ritz-S", s, variant="inner") is False
+    assert P.recycle_dim(0) == 0
+    assert P.recycle_dim(1) == s
+    AH2 = prob.apply_H(1, x2[1], ths[2])
+    U, C, _, _ = orc.refresh_inner(np.zeros((x2[1].size, 0)), V1, AH1, AH2,
+                                   lambda v: prob.Jw(1, x2[1], ths[2], v.reshape(x2[1].shape)), s, "ritz", "S", "R")
+    Ug, Cg = exported(P, 1, np.float64)
+    assert min_cos(Ug, U) > 1 - 1e-8, min_cos(Ug, U)
+    # the cleared pair solves as plain CG next, the refreshed one with its new space
+    w = P.zeros()
+    info = P.hessian_solve(w, recycle=True, tol=1e-7, relative=True, warm_start=False, maxit=2000)
+    g0 = prob.rhs(0, x2[0])
+    ref0 = rcg(prob.apply_H(0, x2[0], ths[2]), g0, np.zeros_like(g0), None, None, tol=1e-7 * np.linalg.norm(g0),
+               maxit=2000)
+    assert abs(info[0]["iters"] - ref0["iters"]) <= 1
