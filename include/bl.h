@@ -262,6 +262,11 @@ bl_status bl_recycle_import(bl_problem* prob, int32_t pair, const void* buf, siz
 /* 1 if the last bl_hessian_solve ran its loop as a CUDA graph (see bl_krylov_opts.graph), else 0. */
 int32_t bl_graph_used(const bl_problem* prob);
 
+/* 1 if the problem's FP32 Hessian action stages its input and field tiles with tensor-memory-access
+ * copies (FP32 Fields-of-Experts problem whose every image width is a multiple of 4, on a driver
+ * that encodes tensor maps), 0 if it runs the generic kernel.  Both compute eq. (2.6) identically. */
+int32_t bl_hvp_tma(const bl_problem* prob);
+
 /* Number of this library's kernel launches since the problem was created (host counter). */
 int64_t bl_launch_count(const bl_problem* prob);
 

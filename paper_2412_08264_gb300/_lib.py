@@ -87,6 +87,7 @@ EXPORTS = {
     "bl_recycle_import": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_size_t]),
     "bl_launch_count": (C.c_int64, [C.c_void_p]),
     "bl_graph_used": (C.c_int32, [C.c_void_p]),
+    "bl_hvp_tma": (C.c_int32, [C.c_void_p]),
     "bl_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "bl_profile_read": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                   C.POINTER(C.c_int64)]),

@@ -245,6 +245,10 @@ class Problem:
     def graph_used(self) -> bool:
         return bool(self.lib.bl_graph_used(self.h))
 
+    def hvp_tma(self) -> bool:
+        """Whether the FP32 Hessian action runs the TMA-staged kernel (else the generic one)."""
+        return bool(self.lib.bl_hvp_tma(self.h))
+
     def launch_count(self) -> int:
         return int(self.lib.bl_launch_count(self.h))
 

@@ -16,7 +16,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libbl.so")
-SOURCES = ["vec.cu", "stencil.cu", "krylov.cu", "recycle.cu", "tsmm.cu", "lbfgs.cu", "problem.cu", "jw_static.cu"]
+SOURCES = ["vec.cu", "stencil.cu", "hvp_tma.cu", "krylov.cu", "recycle.cu", "tsmm.cu", "lbfgs.cu", "problem.cu",
+           "jw_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall"]
 

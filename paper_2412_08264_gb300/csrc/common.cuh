@@ -148,6 +148,14 @@ struct bl_problem {
   int64_t launches = 0;
   int n_tiles = 0, n_chunks = 0, n_jtiles = 0;
   bool vec4 = false;                // every pair's n is a multiple of 4 (16-byte column starts)
+  // TMA-staged FP32 Hessian action: tensor maps per pair for the fields (slot 0) and for each input
+  // buffer the Hessian action is launched on (slots 1..tma_slots), encoded at creation
+  bool tma = false;
+  void* d_tmaps = nullptr;
+  const void* tma_in_ptr[8] = {};
+  int tma_in_mult[8] = {};
+  int tma_slots = 0;
+  int* d_kerr = nullptr;            // error word of bounded device waits (0: none)
 
   bl::PairDev* d_pairs = nullptr;
   bl::TileDev* d_tiles = nullptr;
@@ -262,6 +270,20 @@ bl_status load_theta(bl_problem* P, const double* theta);
 // Raise the dynamic shared-memory limits of the stencil kernels this problem launches (done once at
 // creation, so that graph capture never has to change function attributes).
 bl_status prepare_kernels(bl_problem* P);
+
+// ---- hvp_tma.cu ----
+// Encode the tensor maps of the TMA-staged FP32 Hessian action (sets P->tma when the problem
+// qualifies: FP32 FoE, every width a multiple of 4); prepare its shared-memory limit.
+bl_status hvp_tma_setup(bl_problem* P);
+bl_status prepare_hvp_tma(bl_problem* P);
+// Slot of an input buffer whose tensor maps exist, or -1.
+int hvp_tma_slot(const bl_problem* P, const void* in, int mult);
+bl_status launch_hvp_tma(bl_problem* P, int slot, const void* in, void* out, int mult, int cols, const int* mask);
+// Whether the Krylov loop takes its dot products from the Hessian action's epilogue (tile partials)
+// or from the separate chunk pass (the TMA-staged kernel computes q only).
+inline bool hvp_fused_dots(const bl_problem* P) { return P->reg.kind == BL_REG_FOE && !P->tma; }
+// Read and clear the device error word of bounded waits (synchronises the stream).
+bl_status check_kernel_error(bl_problem* P);
 
 // ---- krylov.cu ----
 bl_status run_hessian_solve(bl_problem* P, const int* mask_host, const bl_krylov_opts* o,

@@ -122,6 +122,44 @@ __device__ __forceinline__ double block_total(const A& acc, double* red) {
   return red[32];
 }
 
+// acc[yy][xx] += sum_{a,b} tap(a, b) src[(yy + a) * ld + xx + b]; tap = k[a][b] or k flipped.
+// ALIGNED: the caller guarantees src and ld are 16-byte multiples, so FP32 row windows whose
+// length is a multiple of 4 are read with 128-bit shared loads.
+template <int F, int BY, int BX, bool FLIP, bool ALIGNED = false, typename T>
+__device__ __forceinline__ void corr_block(const T* __restrict__ src, int ld, const T (&k)[F * F],
+                                           T (&acc)[BY][BX]) {
+  constexpr int NS = BX + F - 1;
+  constexpr bool kVec = ALIGNED && sizeof(T) == 4 && NS % 4 == 0;
+#pragma unroll
+  for (int ry = 0; ry < BY + F - 1; ++ry) {
+    T seg[NS];
+    if constexpr (kVec) {
+#pragma unroll
+      for (int c = 0; c < NS; c += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(&src[ry * ld + c]);
+        seg[c] = v.x;
+        seg[c + 1] = v.y;
+        seg[c + 2] = v.z;
+        seg[c + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < NS; ++c) seg[c] = src[ry * ld + c];
+    }
+#pragma unroll
+    for (int yy = 0; yy < BY; ++yy) {
+      const int a = ry - yy;
+      if (a < 0 || a >= F) continue;
+#pragma unroll
+      for (int b = 0; b < F; ++b) {
+        const T tap = FLIP ? k[(F - 1 - a) * F + (F - 1 - b)] : k[a * F + b];
+#pragma unroll
+        for (int xx = 0; xx < BX; ++xx) acc[yy][xx] = fma(tap, seg[xx + b], acc[yy][xx]);
+      }
+    }
+  }
+}
+
 // Column j of pair `pr` in a batched n x mult matrix (mult = 0: plain batched vector).
 template <typename T>
 __device__ __forceinline__ T* col_ptr(T* base, const PairDev& pr, int mult, int j) {

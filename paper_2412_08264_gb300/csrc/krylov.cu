@@ -775,7 +775,7 @@ static bl_status solve_impl(bl_problem* P, const int* mask_host, const bl_krylov
 
   bl_status st = ensure_cpart(P, (size_t)P->n_chunks * (1 + 2 * P->SMAX));
   if (st != BL_OK) return st;
-  const bool fused = P->reg.kind == BL_REG_FOE;
+  const bool fused = hvp_fused_dots(P);
   if (fused) {
     st = ensure_tpart(P, (size_t)P->n_tiles * (1 + 2 * P->SMAX));
     if (st != BL_OK) return st;
@@ -983,8 +983,10 @@ static bl_status solve_impl(bl_problem* P, const int* mask_host, const bl_krylov
 
 bl_status run_hessian_solve(bl_problem* P, const int* mask_host, const bl_krylov_opts* o, const void* g,
                             const double* nsc_scale, std::vector<bl_solve_info>& info) {
-  return P->prec == BL_FP32 ? solve_impl<float>(P, mask_host, o, g, nsc_scale, info)
-                            : solve_impl<double>(P, mask_host, o, g, nsc_scale, info);
+  const bl_status st = P->prec == BL_FP32 ? solve_impl<float>(P, mask_host, o, g, nsc_scale, info)
+                                          : solve_impl<double>(P, mask_host, o, g, nsc_scale, info);
+  const bl_status ke = check_kernel_error(P);
+  return ke != BL_OK ? ke : st;
 }
 
 }  // namespace bl

@@ -104,6 +104,8 @@ const char* bl_last_error(void) {
 
 int64_t bl_launch_count(const bl_problem* P) { return P ? P->launches : 0; }
 
+int32_t bl_hvp_tma(const bl_problem* P) { return (P && P->tma) ? 1 : 0; }
+
 int32_t bl_graph_used(const bl_problem* P) { return (P && P->graph_used) ? 1 : 0; }
 
 static bl_status prof_collect(bl_problem* P) {
@@ -180,7 +182,8 @@ void bl_problem_destroy(bl_problem* P) {
                   P->d_active, P->d_cols, P->d_flag, P->dG, P->dT, P->dJ, P->dY, P->dY2, P->dY3, P->d_tk,
                   P->lx, P->lg, P->ld, P->lxt, P->lgt, P->lq, P->S, P->Yh, P->lsy, P->lyy, P->lcs, P->lcy,
                   P->lst, P->tpart, P->cpart, P->vals,
-                  P->d_pix, P->d_zero, P->d_loop, P->mv_prev, P->my1, P->my2, P->mrs, P->d_opmask, P->lz_alpha, P->lz_rho, P->lz_c};
+                  P->d_pix, P->d_zero, P->d_loop, P->mv_prev, P->my1, P->my2, P->mrs, P->d_opmask, P->lz_alpha, P->lz_rho, P->lz_c,
+                  P->d_tmaps, P->d_kerr};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (P->h_flag) cudaFreeHost(P->h_flag);
@@ -376,6 +379,7 @@ bl_status bl_problem_create(const bl_pair_desc* pairs, int32_t K, const bl_reg_d
   BL_ALLOC(dalloc((void**)&P->dY3, std::max(4 * tm2, (size_t)K * kMaxHistory) * sizeof(double)));
   BL_ALLOC(dalloc((void**)&P->vals, 8 * (size_t)K * sizeof(double)));
   BL_ALLOC(dalloc((void**)&P->d_pix, BL_KC_COUNT * sizeof(unsigned long long)));
+  BL_ALLOC(dalloc((void**)&P->d_kerr, sizeof(int)));
   if (cudaMallocHost((void**)&P->h_flag, sizeof(int)) != cudaSuccess) {
     bl_problem_destroy(P);
     return fail(BL_ENOMEM, "cudaMallocHost failed");
@@ -397,12 +401,13 @@ bl_status bl_problem_create(const bl_pair_desc* pairs, int32_t K, const bl_reg_d
   e = e == cudaSuccess ? cudaMemsetAsync(P->d_zero, 0, K * sizeof(int), P->stream) : e;
   e = e == cudaSuccess ? cudaMemsetAsync(P->ztc, 0, (size_t)K * P->SMAX * P->SMAX * sizeof(double), P->stream) : e;
   e = e == cudaSuccess ? cudaMemsetAsync(P->xhat, 0, n * P->esz, P->stream) : e;
+  e = e == cudaSuccess ? cudaMemsetAsync(P->d_kerr, 0, sizeof(int), P->stream) : e;
   e = e == cudaSuccess ? cudaStreamSynchronize(P->stream) : e;
   if (e != cudaSuccess) {
     bl_problem_destroy(P);
     return fail(BL_ECUDA, std::string("problem set-up: ") + cudaGetErrorString(e));
   }
-  if ((st = prepare_kernels(P)) != BL_OK) {
+  if ((st = prepare_kernels(P)) != BL_OK || (st = hvp_tma_setup(P)) != BL_OK || (st = prepare_hvp_tma(P)) != BL_OK) {
     bl_problem_destroy(P);
     return st;
   }

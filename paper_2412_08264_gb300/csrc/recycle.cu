@@ -708,7 +708,9 @@ static bl_status refresh_impl(bl_problem* P, const std::vector<int>& mask_host, 
 }
 
 bl_status run_ritz_update(bl_problem* P, const std::vector<int>& mask_host, const bl_recycle_opts* o) {
-  return P->prec == BL_FP32 ? refresh_impl<float>(P, mask_host, o) : refresh_impl<double>(P, mask_host, o);
+  const bl_status st = P->prec == BL_FP32 ? refresh_impl<float>(P, mask_host, o) : refresh_impl<double>(P, mask_host, o);
+  const bl_status ke = check_kernel_error(P);
+  return ke != BL_OK ? ke : st;
 }
 
 }  // namespace bl

@@ -16,44 +16,6 @@
 
 namespace bl {
 
-// acc[yy][xx] += sum_{a,b} tap(a, b) src[(yy + a) * ld + xx + b]; tap = k[a][b] or k flipped.
-// ALIGNED: the caller guarantees src and ld are 16-byte multiples, so FP32 row windows whose
-// length is a multiple of 4 are read with 128-bit shared loads.
-template <int F, int BY, int BX, bool FLIP, bool ALIGNED = false, typename T>
-__device__ __forceinline__ void corr_block(const T* __restrict__ src, int ld, const T (&k)[F * F],
-                                           T (&acc)[BY][BX]) {
-  constexpr int NS = BX + F - 1;
-  constexpr bool kVec = ALIGNED && sizeof(T) == 4 && NS % 4 == 0;
-#pragma unroll
-  for (int ry = 0; ry < BY + F - 1; ++ry) {
-    T seg[NS];
-    if constexpr (kVec) {
-#pragma unroll
-      for (int c = 0; c < NS; c += 4) {
-        const float4 v = *reinterpret_cast<const float4*>(&src[ry * ld + c]);
-        seg[c] = v.x;
-        seg[c + 1] = v.y;
-        seg[c + 2] = v.z;
-        seg[c + 3] = v.w;
-      }
-    } else {
-#pragma unroll
-      for (int c = 0; c < NS; ++c) seg[c] = src[ry * ld + c];
-    }
-#pragma unroll
-    for (int yy = 0; yy < BY; ++yy) {
-      const int a = ry - yy;
-      if (a < 0 || a >= F) continue;
-#pragma unroll
-      for (int b = 0; b < F; ++b) {
-        const T tap = FLIP ? k[(F - 1 - a) * F + (F - 1 - b)] : k[a * F + b];
-#pragma unroll
-        for (int xx = 0; xx < BX; ++xx) acc[yy][xx] = fma(tap, seg[xx + b], acc[yy][xx]);
-      }
-    }
-  }
-}
-
 // Asynchronous global -> shared copies of single elements (cp.async, L1-allocating).
 template <typename T>
 __device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
@@ -764,6 +726,10 @@ template <typename T>
 static bl_status hvp_foe(bl_problem* P, const void* in, void* out, int mult, int cols, const int* mask,
                          const int* dots_s, const int* dots_hz) {
   const bool dots = dots_s != nullptr;
+  if (sizeof(T) == 4 && !dots) {
+    const int slot = hvp_tma_slot(P, in, mult);
+    if (slot >= 0) return launch_hvp_tma(P, slot, in, out, mult, cols, mask);
+  }
   StencilArgs<T> a{};
   a.pairs = P->d_pairs;
   a.tiles = P->d_tiles;

@@ -35,6 +35,16 @@ ProfScope::~ProfScope() {
 
 unsigned long long* pix_counter(bl_problem* P, int cls) { return P->prof ? P->d_pix + cls : nullptr; }
 
+bl_status check_kernel_error(bl_problem* P) {
+  int code = 0;
+  BL_CUDA_TRY(cudaMemcpyAsync(&code, P->d_kerr, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+  BL_CUDA_TRY(cudaStreamSynchronize(P->stream));
+  if (code == 0) return BL_OK;
+  BL_CUDA_TRY(cudaMemsetAsync(P->d_kerr, 0, sizeof(int), P->stream));
+  return fail(BL_ECUDA, "a Hessian-action kernel gave up waiting for its tile copies (code " + std::to_string(code) +
+                            "); its results are invalid");
+}
+
 bl_status dalloc(void** ptr, size_t bytes) {
   *ptr = nullptr;
   if (bytes == 0) bytes = 16;

@@ -17,9 +17,16 @@ pytestmark = pytest.mark.gpu
 TOL = {"fp32": 1e-5, "fp64": 1e-12}
 
 
-def mixed_workload(seed=0, phi="sq", reg="foe"):
-    """Three inpainting pairs (30 % kept) and one blur pair."""
-    if reg == "tv":
+def mixed_workload(seed=0, phi="sq", reg="foe", widths4=False):
+    """Three inpainting pairs (30 % kept) and one blur pair (widths4: every width a multiple of 4, so
+    the FP32 Hessian action runs the TMA-staged kernel)."""
+    if widths4:
+        wl = synth.Workload("mixed_inpaint4", [synth.PairSpec(28, 28, 1.0, 0, 0.1, 0.3),
+                                               synth.PairSpec(70, 132, 1.0, 0, 0.1, 0.3),
+                                               synth.PairSpec(37, 44, 1.0, 0, 0.1, 0.5),
+                                               synth.PairSpec(40, 52, 1.7, 3, 0.02)],
+                            reg="foe", n_filters=3, filter_size=5, phi=phi, recycle_dim=8)
+    elif reg == "tv":
         wl = synth.tv_32()
         wl.pairs = [synth.PairSpec(28, 28, 1.0, 0, 0.1, 0.3), synth.PairSpec(70, 131, 1.0, 0, 0.1, 0.3),
                     synth.PairSpec(13, 21, 1.2, 1, 0.01)]
@@ -49,11 +56,13 @@ def test_forward_mask(precision):
             assert np.all(got[ll.mask == 0] == 0)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+@pytest.mark.parametrize("precision, widths4", [("fp32", False), ("fp64", False), ("fp32", True)],
+                         ids=["fp32", "fp64", "fp32-tma"])
 @pytest.mark.parametrize("phi", ["sq", "charbonnier"])
-def test_hvp_gradient_value_parity_mask(precision, phi):
-    wl = mixed_workload(seed=1, phi=phi)
+def test_hvp_gradient_value_parity_mask(precision, phi, widths4):
+    wl = mixed_workload(seed=1, phi=phi, widths4=widths4)
     P, prob, dt = make(wl, precision)
+    assert P.hvp_tma() == widths4
     rng = np.random.default_rng(1)
     xs = point(wl, rng)
     th0 = r32(wl.theta0) if precision == "fp32" else wl.theta0

@@ -25,10 +25,14 @@ def small_wl(sizes=((48, 52), (33, 70)), N=3, f=5, rb=2, seed=1):
     return synth.uneven_foe(list(sizes), n_filters=N, f=f, blur_radius=rb, seed=seed)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_plain_cg_matches_checker(precision):
-    wl = small_wl()
+@pytest.mark.parametrize("precision, sizes", [("fp64", ((48, 52), (33, 70))), ("fp32", ((48, 52), (33, 70))),
+                                              ("fp32", ((48, 52), (33, 72)))], ids=["fp64", "fp32", "fp32-tma"])
+def test_plain_cg_matches_checker(precision, sizes):
+    """fp32-tma: every width a multiple of 4, so the Hessian action runs the TMA-staged kernel and the
+    Krylov dot products come from the separate chunk pass."""
+    wl = small_wl(sizes=sizes)
     P, prob, dt = make(wl, precision, max_recycle=4, max_basis=60)
+    assert P.hvp_tma() == (precision == "fp32" and all(w % 4 == 0 for _, w in sizes))
     th = r32(wl.theta0) if precision == "fp32" else wl.theta0
     xs = [r32(x) for x in lower_points(prob, th)] if precision == "fp32" else lower_points(prob, th)
     P.set_point(torch.tensor(th, dtype=torch.float64, device=DEV), packed(xs, dt))
@@ -93,24 +97,28 @@ def test_recycled_sequence_fp64_matches_checker():
         th = th - 0.05 * rng.standard_normal(th.shape) * 0.1
 
 
-@pytest.mark.parametrize("sizes", [((64, 64), (40, 90)), ((37, 45), (100, 123))], ids=["aligned", "ragged"])
+@pytest.mark.parametrize("sizes", [((64, 64), (40, 90)), ((37, 45), (100, 123)), ((64, 64), (41, 92))],
+                         ids=["aligned", "ragged", "tma"])
 def test_refresh_invariants_fp32(sizes):
     """After bl_ritz_update: C = H U and C^T C = I on the exported recycle space (Section 2.2.2).
     "aligned": every image a multiple of 4 pixels (16-byte staging of the tall-skinny kernels);
-    "ragged": odd sizes and an image spanning several 4096-pixel chunks with a short tail."""
+    "ragged": odd sizes and an image spanning several 4096-pixel chunks with a short tail;
+    "tma": every width a multiple of 4, so the refresh's multi-column Hessian actions (on W~ and U)
+    run the TMA-staged kernel."""
     wl = small_wl(sizes=sizes, N=4, seed=7)
     P, prob, dt = make(wl, "fp32", max_recycle=8, max_basis=60)
+    assert P.hvp_tma() == all(w % 4 == 0 for _, w in sizes)
     th = r32(wl.theta0)
     xs = [r32(x) for x in lower_points(prob, th, gtol=1e-8)]
     theta = torch.tensor(th, dtype=torch.float64, device=DEV)
     P.set_point(theta, packed(xs, dt))
     w = P.zeros()
     P.hessian_solve(w, recycle=True, tol=1e-5, store_basis=True)
-    for kind in ["Ritz-S", "RGen-L(R)", "HRitz-L"]:
+    for kind, variant in [("Ritz-S", "outer"), ("RGen-L(R)", "outer"), ("HRitz-L", "outer"), ("Ritz-S", "inner")]:
         P.set_point(theta, packed(xs, dt))
         w2 = P.zeros()
-        P.hessian_solve(w2, recycle=False, tol=1e-5, store_basis=True)
-        P.ritz_update(kind, 8)
+        P.hessian_solve(w2, recycle=False, tol=1e-5, store_basis="lanczos" if variant == "inner" else True)
+        P.ritz_update(kind, 8, variant=variant)
         for k in range(P.K):
             s = P.recycle_dim(k)
             assert s == 8
@@ -242,3 +250,4 @@ def test_graph_loop_matches_stream_loop():
     for iters, w in outs[1:]:
         assert iters == outs[0][0]
         assert np.array_equal(w, outs[0][1])
+

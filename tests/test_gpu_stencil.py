@@ -7,7 +7,7 @@ import torch
 
 from paper_2412_08264_gb300 import synth
 from oracle import operators as ops
-from tests.gpu_util import DEV, make, packed, r32, rel, split
+from tests.gpu_util import DEV, make, max_elem, packed, r32, rel, split
 
 pytestmark = pytest.mark.gpu
 
@@ -59,6 +59,42 @@ def test_hvp_parity(case, precision):
     for k, ll in enumerate(prob.lowers):
         ref = ll.hvp(xs[k], th0, vs[k])
         assert rel(out[k], ref) < TOL[precision], (k, rel(out[k], ref))
+        assert max_elem(out[k], ref) < TOL[precision], (k, max_elem(out[k], ref))
+
+
+# Every width a multiple of 4: the FP32 Hessian action runs the TMA-staged kernel.  Several tiles,
+# ragged tails in both directions, images narrower and shorter than one tile, every blur radius.
+TMA_CASES = [
+    # (sizes, n_filters, f, blur_radius)
+    ([(70, 132), (37, 44), (9, 4)], 3, 5, 2),
+    ([(128, 192), (67, 60)], 16, 5, 4),
+    ([(61, 76), (130, 64)], 2, 7, 3),
+    ([(64, 64), (5, 8)], 2, 1, 4),
+    ([(45, 124)], 4, 3, 1),
+    ([(33, 68), (120, 4)], 2, 5, 0),
+]
+
+
+@pytest.mark.parametrize("case", range(len(TMA_CASES)))
+def test_hvp_parity_tma_path(case):
+    """The TMA-staged FP32 Hessian action against the checker, per element (tile seams, image borders,
+    the zero-filled halo of the tensor copies) and in norm."""
+    sizes, N, f, rb = TMA_CASES[case]
+    wl = workload(sizes, N, f, rb, seed=40 + case)
+    P, prob, dt = make(wl, "fp32")
+    assert P.hvp_tma()
+    rng = np.random.default_rng(40 + case)
+    xs = point(prob, wl, rng)
+    th0 = r32(wl.theta0)
+    theta = torch.tensor(th0, dtype=torch.float64, device=DEV)
+    P.set_point(theta, packed(xs, dt))
+    for rep in range(2):
+        vs = [r32(rng.standard_normal(x.shape)) for x in xs]
+        out = split(P.hvp(packed(vs, dt)), P.sizes)
+        for k, ll in enumerate(prob.lowers):
+            ref = ll.hvp(xs[k], th0, vs[k])
+            assert rel(out[k], ref) < TOL["fp32"], (k, rel(out[k], ref))
+            assert max_elem(out[k], ref) < TOL["fp32"], (k, max_elem(out[k], ref))
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
