@@ -251,11 +251,16 @@ bl_status bl_hypergrad(bl_problem* prob, const int32_t* pairs, int32_t npairs, c
 int32_t bl_recycle_dim(const bl_problem* prob, int32_t pair);
 int32_t bl_basis_size(const bl_problem* prob, int32_t pair);
 
-/* Checkpoint of one pair's recycle state (U, C, Z, Z^T C and sizes) to a host buffer.
+/* Checkpoint of one pair's recycle state to a host buffer: U, C, Z, Z^T C and sizes, then the stored
+ * Krylov basis the next bl_ritz_update would read (its columns in storage order and, for a
+ * BL_STORE_LANCZOS record, the CG coefficients), so that a run resumed from the checkpoint continues
+ * exactly as the uninterrupted one (layout version 2; version-1 buffers, without the basis, are
+ * still accepted and leave the pair without a stored basis).
  * bl_recycle_export: with buf == NULL sets *bytes to the size needed; otherwise writes
  * at most *bytes (BL_EINVAL if too small) and sets *bytes to the size written.
  * bl_recycle_import: restores a buffer written by bl_recycle_export for a pair of the same
- * size and precision (BL_EINVAL on any header mismatch or truncation). */
+ * size and precision, and (version 2) a problem with the same max_recycle and max_basis
+ * (BL_EINVAL on any header mismatch or truncation). */
 bl_status bl_recycle_export(bl_problem* prob, int32_t pair, void* buf, size_t* bytes);
 bl_status bl_recycle_import(bl_problem* prob, int32_t pair, const void* buf, size_t bytes);
 
@@ -266,6 +271,16 @@ int32_t bl_graph_used(const bl_problem* prob);
  * copies (FP32 Fields-of-Experts problem whose every image width is a multiple of 4, on a driver
  * that encodes tensor maps), 0 if it runs the generic kernel.  Both compute eq. (2.6) identically. */
 int32_t bl_hvp_tma(const bl_problem* prob);
+
+/* Output tile side of the TMA-staged Hessian action for one pair (0 if the generic kernel runs).
+ * At creation the library times its tile variants per image-size class (height, width, blur radius,
+ * operator) and keeps the faster: tile_out(f) (60 x 60 for 3 x 3 and 5 x 5 filters, 56 for 7 x 7, 64 for
+ * 1 x 1) or, for 3 x 3 and 5 x 5 filters, 64 x 64.  Both compute eq. (2.6) identically. */
+int32_t bl_hvp_tile(const bl_problem* prob, int32_t pair);
+/* Force a pair's tile variant by its side (one that bl_hvp_tile can return for this filter size);
+ * BL_EINVAL otherwise, or when the problem runs the generic kernel.  Synchronises the stream and
+ * drops the captured Krylov-loop graph. */
+bl_status bl_set_hvp_tile(bl_problem* prob, int32_t pair, int32_t side);
 
 /* Number of this library's kernel launches since the problem was created (host counter). */
 int64_t bl_launch_count(const bl_problem* prob);
@@ -285,11 +300,16 @@ typedef enum {
   BL_KC_GEMM = 7,       /* tall-skinny basis products */
   BL_KC_DENSE = 8,      /* small FP64 eigen / Cholesky problems */
   BL_KC_OTHER = 9,      /* reductions, fields, copies */
-  BL_KC_COUNT = 10
+  BL_KC_KRYLOV_VEC = 10,/* recycled-CG vector passes (dot products, updates), bytes counted */
+  BL_KC_COUNT = 11
 } bl_kernel_class;
 bl_status bl_profile_enable(bl_problem* prob, int32_t enable);
 bl_status bl_profile_read(bl_problem* prob, int32_t kernel_class, double* total_ms, int64_t* launches,
                           int64_t* pixels);
+/* Algorithmic global-memory bytes (each vector read or written once per pass) moved by the kernels of
+ * one class since bl_profile_enable, counted by the kernels themselves; 0 for classes that do not
+ * count bytes (only BL_KC_KRYLOV_VEC does).  Synchronises the stream. */
+bl_status bl_profile_read_bytes(bl_problem* prob, int32_t kernel_class, int64_t* bytes);
 
 const char* bl_last_error(void);
 

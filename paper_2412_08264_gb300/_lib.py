@@ -25,7 +25,8 @@ BL_SIZE = {"S": 0, "L": 1, "M": 2}
 BL_SIDE = {"R": 0, "L": 1, "M": 2}
 BL_REFRESH = {"outer": 0, "inner": 1}
 BL_STORE_NONE, BL_STORE_RECENT, BL_STORE_LANCZOS = 0, 1, 2
-KERNEL_CLASSES = ["hvp", "hvp_multi", "grad", "jw", "krylov", "lbfgs", "gram", "gemm", "dense", "other"]
+KERNEL_CLASSES = ["hvp", "hvp_multi", "grad", "jw", "krylov", "lbfgs", "gram", "gemm", "dense", "other",
+                  "krylov_vec"]
 
 
 class PairDesc(C.Structure):
@@ -88,9 +89,12 @@ EXPORTS = {
     "bl_launch_count": (C.c_int64, [C.c_void_p]),
     "bl_graph_used": (C.c_int32, [C.c_void_p]),
     "bl_hvp_tma": (C.c_int32, [C.c_void_p]),
+    "bl_hvp_tile": (C.c_int32, [C.c_void_p, C.c_int32]),
+    "bl_set_hvp_tile": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
     "bl_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "bl_profile_read": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                   C.POINTER(C.c_int64)]),
+    "bl_profile_read_bytes": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int64)]),
     "bl_last_error": (C.c_char_p, []),
     "bl_jw_fp32_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_int32,
                                     C.c_int32, C.c_int32, C.c_double, C.c_void_p, C.c_void_p]),

@@ -249,6 +249,13 @@ class Problem:
         """Whether the FP32 Hessian action runs the TMA-staged kernel (else the generic one)."""
         return bool(self.lib.bl_hvp_tma(self.h))
 
+    def hvp_tile(self, pair: int) -> int:
+        """Output tile side of the TMA-staged Hessian action for a pair (0: generic kernel)."""
+        return int(self.lib.bl_hvp_tile(self.h, int(pair)))
+
+    def set_hvp_tile(self, pair: int, side: int):
+        L.check(self.lib.bl_set_hvp_tile(self.h, int(pair), int(side)), "bl_set_hvp_tile")
+
     def launch_count(self) -> int:
         return int(self.lib.bl_launch_count(self.h))
 
@@ -256,12 +263,15 @@ class Problem:
         L.check(self.lib.bl_profile_enable(self.h, 1 if enable else 0), "bl_profile_enable")
 
     def profile_read(self) -> dict:
-        """Per kernel class: total milliseconds, launches and pixels processed since profile()."""
+        """Per kernel class: total milliseconds, launches, pixels processed and (vector passes) algorithmic
+        bytes moved since profile()."""
         out = {}
         for i, name in enumerate(L.KERNEL_CLASSES):
             ms, n, px = C.c_double(), C.c_int64(), C.c_int64()
             L.check(self.lib.bl_profile_read(self.h, i, C.byref(ms), C.byref(n), C.byref(px)), "bl_profile_read")
-            out[name] = dict(ms=ms.value, launches=n.value, pixels=px.value)
+            nb = C.c_int64()
+            L.check(self.lib.bl_profile_read_bytes(self.h, i, C.byref(nb)), "bl_profile_read_bytes")
+            out[name] = dict(ms=ms.value, launches=n.value, pixels=px.value, bytes=nb.value)
         return out
 
 

@@ -57,6 +57,7 @@ __host__ __device__ constexpr int jw_tile_out(int F) { return sizeof(T) == 4 ? 6
 constexpr int kUnitChunks = 0;
 constexpr int kUnitTiles = 1;
 constexpr int kUnitJwTiles = 2;
+constexpr int kUnitHTiles = 3;
 
 struct PairDev {
   int h, w;
@@ -66,11 +67,14 @@ struct PairDev {
   int tbeg, tend;      // tiles [tbeg, tend) of this pair
   int jtbeg, jtend;    // J w tiles [jtbeg, jtend)
   int cbeg, cend;      // chunks [cbeg, cend)
+  int htbeg, htend;    // tiles [htbeg, htend) of the TMA-staged kernels' list
   float gf[2 * BL_MAX_BLUR_RADIUS + 1];
   double gd[2 * BL_MAX_BLUR_RADIUS + 1];
 };
 
 struct TileDev { int pair, oy, ox; };
+// Tile of the TMA-staged Hessian action: var selects the tile geometry (0: tile_out(F), 1: 64 x 64)
+struct HTileDev { int pair, oy, ox, var; };
 struct ChunkDev { int pair; long long start; int len; };
 
 // Per-pair scalar state of a Krylov solve (FP64 recurrences).
@@ -155,6 +159,11 @@ struct bl_problem {
   const void* tma_in_ptr[8] = {};
   int tma_in_mult[8] = {};
   int tma_slots = 0;
+  int tma_nvar = 0;                 // tile variants with encoded maps
+  bl::HTileDev* d_htiles = nullptr; // tile list of the TMA-staged Hessian action
+  int n_htiles = 0, htiles_cap = 0;
+  std::vector<int> hvar;            // per pair: its tile variant
+  std::vector<bl::PairDev> pd_host; // host copy of d_pairs (the H tile ranges change after tuning)
   int* d_kerr = nullptr;            // error word of bounded device waits (0: none)
 
   bl::PairDev* d_pairs = nullptr;
@@ -224,6 +233,7 @@ struct bl_problem {
   double prof_ms[BL_KC_COUNT] = {};
   int64_t prof_n[BL_KC_COUNT] = {};
   unsigned long long* d_pix = nullptr;   // BL_KC_COUNT counters
+  unsigned long long* d_bytes = nullptr; // BL_KC_COUNT algorithmic byte counters
 
   // partial sums
   double* tpart = nullptr;
@@ -243,6 +253,7 @@ struct ProfScope {
   ~ProfScope();
 };
 unsigned long long* pix_counter(bl_problem* P, int cls);   // null when profiling is off
+unsigned long long* bytes_counter(bl_problem* P, int cls); // null when profiling is off
 
 // Allocation helper (tracks nothing; caller frees in bl_problem_destroy).
 bl_status dalloc(void** ptr, size_t bytes);
@@ -279,6 +290,14 @@ bl_status prepare_hvp_tma(bl_problem* P);
 // Slot of an input buffer whose tensor maps exist, or -1.
 int hvp_tma_slot(const bl_problem* P, const void* in, int mult);
 bl_status launch_hvp_tma(bl_problem* P, int slot, const void* in, void* out, int mult, int cols, const int* mask);
+// Gradient and value partials of Phi (eq. (5.1)) by the TMA-staged kernel; false-free: returns -1 from
+// hvp_tma_grad_slot when the input buffer has no tensor maps (the generic kernel runs then).
+int hvp_tma_grad_slot(const bl_problem* P, const void* x);
+bl_status launch_grad_tma(bl_problem* P, int slot, void* grad, const int* mask, double* tpart);
+// Output tile side of the TMA-staged Hessian action for one pair (0 when the generic kernel runs), and
+// forcing a pair's tile variant (tests check every variant).
+int hvp_tma_tile(const bl_problem* P, int pair);
+bl_status hvp_tma_force_tile(bl_problem* P, int pair, int side);
 // Whether the Krylov loop takes its dot products from the Hessian action's epilogue (tile partials)
 // or from the separate chunk pass (the TMA-staged kernel computes q only).
 inline bool hvp_fused_dots(const bl_problem* P) { return P->reg.kind == BL_REG_FOE && !P->tma; }

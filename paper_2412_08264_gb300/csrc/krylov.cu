@@ -50,6 +50,7 @@ struct KrylovArgs {
   // CG Lanczos record (BL_STORE_LANCZOS): alpha_j, rho_j (K x KMAX), C^T H p_j (K x KMAX x SMAX)
   int lanczos;
   double *lz_alpha, *lz_rho, *lz_c;
+  unsigned long long* nbytes;   // algorithmic bytes of the vector passes (profiling), or null
 };
 
 // Per-chunk partial sums of up to 64 components, one warp total each, written to part[chunk][off + m].
@@ -267,6 +268,50 @@ __global__ void k_dots(KrylovArgs a, const T* p, const T* q, const T* C, const T
   }
 }
 
+// The same partials for FP32 problems whose images are multiples of 4 pixels (16-byte aligned column
+// starts): one warp per component streams its column of the chunk with 128-bit loads, eight in
+// flight per lane, against q (re-read from L1), so no barrier separates the components.
+__global__ void k_dots_v4(KrylovArgs a, const float* p, const float* q, const float* C, const float* Z) {
+  const ChunkDev ch = a.chunks[blockIdx.x];
+  if (!a.st[ch.pair].active) return;
+  const PairDev pr = a.pairs[ch.pair];
+  const int s = a.s_k[ch.pair];
+  const int nz = a.hasz[ch.pair] ? s : 0;
+  const int ncomp = 1 + 2 * a.SMAX;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (a.nbytes && threadIdx.x == 0) atomicAdd(a.nbytes, (unsigned long long)ch.len * 4ull * (2 + s + nz));
+  const int nv = ch.len >> 2;                                  // chunk lengths are multiples of 4
+  const float4* q4 = reinterpret_cast<const float4*>(q + pr.off + ch.start);
+  for (int comp = wid; comp < 1 + s + nz; comp += nw) {
+    const float* src = comp == 0 ? p + pr.off
+                                 : (comp <= s ? C + pr.off * a.SMAX + (long long)(comp - 1) * pr.n
+                                              : Z + pr.off * a.SMAX + (long long)(comp - 1 - s) * pr.n);
+    const float4* s4 = reinterpret_cast<const float4*>(src + ch.start);
+    Accum<float> acc;
+    for (int i0 = 0; i0 < nv; i0 += 32 * 8) {
+      float4 u[8], v[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int i = i0 + j * 32 + lane;
+        u[j] = i < nv ? s4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        v[j] = i < nv ? q4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        acc.add(u[j].x * v[j].x);
+        acc.add(u[j].y * v[j].y);
+        acc.add(u[j].z * v[j].z);
+        acc.add(u[j].w * v[j].w);
+      }
+    }
+    const double tot = warp_total(acc);
+    if (lane == 0) {
+      const int slot = comp <= s ? comp : comp - s + a.SMAX;
+      a.cpart[(size_t)blockIdx.x * ncomp + slot] = tot;
+    }
+  }
+}
+
 // alpha, c = C^T q, z -= alpha c; breakdown check
 __global__ void k_scalar1(KrylovArgs a, int use_tiles) {
   __shared__ double sh[65];
@@ -328,6 +373,10 @@ __global__ void k_update(KrylovArgs a, T* w, T* r, const T* p, const T* q, const
   __syncthreads();
   const T* Cb = C + pr.off * a.SMAX;
   const T* Zb = Z + pr.off * a.SMAX;
+  if (a.nbytes && threadIdx.x == 0) {
+    const int stored = (store == 1 || (store == 2 && S.iters < a.KMAX)) ? 1 : 0;
+    atomicAdd(a.nbytes, (unsigned long long)ch.len * sizeof(T) * (4 + s + nz + 2 + stored));
+  }
   // store 1: ring of the most recent KMAX residuals; store 2: the first KMAX (Lanczos record)
   const bool st_now = store == 1 || (store == 2 && S.iters < a.KMAX);
   T* Vc = st_now ? V + pr.off * a.KMAX + (long long)(S.iters % a.KMAX) * pr.n : nullptr;
@@ -354,6 +403,92 @@ __global__ void k_update(KrylovArgs a, T* w, T* r, const T* p, const T* q, const
     for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
       const long long li = ch.start + t;
       acc.add(Zb[(long long)m * pr.n + li] * r[pr.off + li]);
+    }
+    const double v = warp_total(acc);
+    if (lane == 0) red[wid * 65 + 1 + (m & 63)] = v;
+    if ((m & 63) == 63 || m == nz - 1) {
+      __syncthreads();
+      const int base = (m & ~63);
+      flush_components<kChunkThreads>(red + 1, m - base + 1, a.cpart + (size_t)blockIdx.x * ncomp + 1 + base);
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  flush_components<kChunkThreads>(red, 1, a.cpart + (size_t)blockIdx.x * ncomp);
+}
+
+// The update pass for FP32 problems whose images are multiples of 4 pixels: each thread moves float4
+// items (16-byte loads and stores), the C columns of an item loaded together before their products.
+__global__ void k_update_v4(KrylovArgs a, float* w, float* r, const float* p, const float* q, const float* C,
+                            const float* Z, float* V, int store, int nsc) {
+  __shared__ double red[8 * 65];
+  __shared__ float cs[64];
+  const ChunkDev ch = a.chunks[blockIdx.x];
+  const SolveState S = a.st[ch.pair];
+  if (!S.active) return;
+  const PairDev pr = a.pairs[ch.pair];
+  const int s = a.s_k[ch.pair];
+  const int nz = (nsc && a.hasz[ch.pair]) ? s : 0;
+  const int ncomp = 1 + a.SMAX;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if ((int)threadIdx.x < s) cs[threadIdx.x] = (float)a.c[ch.pair * a.SMAX + threadIdx.x];
+  __syncthreads();
+  const bool st_now = store == 1 || (store == 2 && S.iters < a.KMAX);
+  if (a.nbytes && threadIdx.x == 0)
+    atomicAdd(a.nbytes, (unsigned long long)ch.len * 4ull * (4 + s + nz + 2 + (st_now ? 1 : 0)));
+  const long long g0 = pr.off + ch.start;
+  const int nv = ch.len >> 2;
+  float4* r4 = reinterpret_cast<float4*>(r + g0);
+  float4* w4 = reinterpret_cast<float4*>(w + g0);
+  const float4* p4 = reinterpret_cast<const float4*>(p + g0);
+  const float4* q4 = reinterpret_cast<const float4*>(q + g0);
+  const float* Cb = C + pr.off * a.SMAX + ch.start;
+  float4* V4 = st_now ? reinterpret_cast<float4*>(V + pr.off * a.KMAX + (long long)(S.iters % a.KMAX) * pr.n +
+                                                  ch.start)
+                      : nullptr;
+  const float inv_nr = (float)(1.0 / sqrt(S.rho));
+  const float al = (float)S.alpha;
+  Accum<float> rho;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    const float4 ro = r4[i], pv = p4[i], qv = q4[i];
+    float4 wv = w4[i];
+    if (V4) V4[i] = make_float4(ro.x * inv_nr, ro.y * inv_nr, ro.z * inv_nr, ro.w * inv_nr);
+    wv.x = fmaf(al, pv.x, wv.x);
+    wv.y = fmaf(al, pv.y, wv.y);
+    wv.z = fmaf(al, pv.z, wv.z);
+    wv.w = fmaf(al, pv.w, wv.w);
+    w4[i] = wv;
+    float4 cc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 8
+    for (int j = 0; j < s; ++j) {
+      const float4 cv = reinterpret_cast<const float4*>(Cb + (long long)j * pr.n)[i];
+      cc.x = fmaf(cs[j], cv.x, cc.x);
+      cc.y = fmaf(cs[j], cv.y, cc.y);
+      cc.z = fmaf(cs[j], cv.z, cc.z);
+      cc.w = fmaf(cs[j], cv.w, cc.w);
+    }
+    const float4 rn = make_float4(ro.x - al * (qv.x - cc.x), ro.y - al * (qv.y - cc.y), ro.z - al * (qv.z - cc.z),
+                                  ro.w - al * (qv.w - cc.w));
+    r4[i] = rn;
+    rho.add(rn.x * rn.x);
+    rho.add(rn.y * rn.y);
+    rho.add(rn.z * rn.z);
+    rho.add(rn.w * rn.w);
+  }
+  {
+    const double v = warp_total(rho);
+    if (lane == 0) red[wid * 65] = v;
+  }
+  const float* Zb = Z + pr.off * a.SMAX + ch.start;
+  for (int m = 0; m < nz; ++m) {
+    Accum<float> acc;
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+      const float4 zv = reinterpret_cast<const float4*>(Zb + (long long)m * pr.n)[i];
+      const float4 rv = r4[i];
+      acc.add(zv.x * rv.x);
+      acc.add(zv.y * rv.y);
+      acc.add(zv.z * rv.z);
+      acc.add(zv.w * rv.w);
     }
     const double v = warp_total(acc);
     if (lane == 0) red[wid * 65 + 1 + (m & 63)] = v;
@@ -422,6 +557,7 @@ __global__ void k_pupdate(KrylovArgs a, const T* r, T* p) {
   if (!S.active) return;
   const PairDev pr = a.pairs[ch.pair];
   const T be = (T)S.beta;
+  if (a.nbytes && threadIdx.x == 0) atomicAdd(a.nbytes, (unsigned long long)ch.len * sizeof(T) * 3);
   for (int t = threadIdx.x; t < ch.len; t += blockDim.x) {
     const long long gi = pr.off + ch.start + t;
     p[gi] = fma(be, p[gi], r[gi]);
@@ -801,6 +937,7 @@ static bl_status solve_impl(bl_problem* P, const int* mask_host, const bl_krylov
   a.lz_alpha = P->lz_alpha;
   a.lz_rho = P->lz_rho;
   a.lz_c = P->lz_c;
+  a.nbytes = bytes_counter(P, BL_KC_KRYLOV_VEC);
   if (minres) {
     const size_t ks = (size_t)K * std::max(P->SMAX, 1);
     a.b1 = P->mrs;
@@ -850,6 +987,18 @@ static bl_status solve_impl(bl_problem* P, const int* mask_host, const bl_krylov
   int* d_itmask = P->d_active + K; // per-pair active copy for the stencil mask
   const int store = P->KMAX > 0 ? (o->store_basis == BL_STORE_LANCZOS ? 2 : (o->store_basis ? 1 : 0)) : 0;
   const int nsc = o->stop == BL_STOP_NSC ? 1 : 0;
+  // dot products of the unfused path: one warp per component for aligned FP32 problems
+  auto launch_dots = [&](const KrylovArgs& a0) -> bl_status {
+    if (sizeof(T) == 4 && P->vec4)
+      k_dots_v4<<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a0, (const float*)(const void*)p,
+                                                               (const float*)(const void*)q,
+                                                               (const float*)(const void*)C,
+                                                               (const float*)(const void*)Z);
+    else
+      k_dots<T><<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a0, p, q, C, Z);
+    BL_LAUNCH_CHECK(P);
+    return BL_OK;
+  };
   auto iteration = [&]() -> bl_status {
     {
       ProfScope ps(P, BL_KC_KRYLOV);
@@ -858,22 +1007,41 @@ static bl_status solve_impl(bl_problem* P, const int* mask_host, const bl_krylov
     }
     bl_status s2 = launch_hvp(P, p, q, 0, 0, d_itmask, fused ? d_seff : nullptr, fused ? d_nohz : nullptr);
     if (s2 != BL_OK) return s2;
-    ProfScope ps(P, BL_KC_KRYLOV);
     if (!fused) {
+      ProfScope ps(P, BL_KC_KRYLOV_VEC);
       KrylovArgs a0 = a;
       a0.hasz = d_nohz;   // the NSC sums come from the update pass
-      k_dots<T><<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a0, p, q, C, Z);
+      if ((s2 = launch_dots(a0)) != BL_OK) return s2;
+    }
+    {
+      ProfScope ps(P, BL_KC_KRYLOV);
+      k_scalar1<<<K, 128, 0, P->stream>>>(a, fused ? 1 : 0);
       BL_LAUNCH_CHECK(P);
     }
-    k_scalar1<<<K, 128, 0, P->stream>>>(a, fused ? 1 : 0);
-    BL_LAUNCH_CHECK(P);
-    k_update<T><<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a, w, r, p, q, C, Z, (T*)P->V, store, nsc);
-    BL_LAUNCH_CHECK(P);
-    BL_CUDA_TRY(cudaMemsetAsync(P->d_flag, 0, sizeof(int), P->stream));
-    k_scalar2<<<K, 32, 0, P->stream>>>(a, nsc, P->d_flag);
-    BL_LAUNCH_CHECK(P);
-    k_pupdate<T><<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a, r, p);
-    BL_LAUNCH_CHECK(P);
+    {
+      ProfScope ps(P, BL_KC_KRYLOV_VEC);
+      if (sizeof(T) == 4 && P->vec4)
+        k_update_v4<<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a, (float*)(void*)w, (float*)(void*)r,
+                                                                   (const float*)(const void*)p,
+                                                                   (const float*)(const void*)q,
+                                                                   (const float*)(const void*)C,
+                                                                   (const float*)(const void*)Z, (float*)P->V, store,
+                                                                   nsc);
+      else
+        k_update<T><<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a, w, r, p, q, C, Z, (T*)P->V, store, nsc);
+      BL_LAUNCH_CHECK(P);
+    }
+    {
+      ProfScope ps(P, BL_KC_KRYLOV);
+      BL_CUDA_TRY(cudaMemsetAsync(P->d_flag, 0, sizeof(int), P->stream));
+      k_scalar2<<<K, 32, 0, P->stream>>>(a, nsc, P->d_flag);
+      BL_LAUNCH_CHECK(P);
+    }
+    {
+      ProfScope ps(P, BL_KC_KRYLOV_VEC);
+      k_pupdate<T><<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a, r, p);
+      BL_LAUNCH_CHECK(P);
+    }
     return BL_OK;
   };
   // MINRES step: q = H v_k (with v^T q, C^T q and, for the NSC rule, Z^T q), Lanczos vector,
@@ -891,8 +1059,7 @@ static bl_status solve_impl(bl_problem* P, const int* mask_host, const bl_krylov
     if (!fused) {
       KrylovArgs a0 = a;
       a0.hasz = zflags;
-      k_dots<T><<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a0, p, q, C, Z);
-      BL_LAUNCH_CHECK(P);
+      if ((s2 = launch_dots(a0)) != BL_OK) return s2;
     }
     k_mr_scalar1<<<K, 128, 0, P->stream>>>(a, fused ? 1 : 0, nsc);
     BL_LAUNCH_CHECK(P);

@@ -106,6 +106,13 @@ int64_t bl_launch_count(const bl_problem* P) { return P ? P->launches : 0; }
 
 int32_t bl_hvp_tma(const bl_problem* P) { return (P && P->tma) ? 1 : 0; }
 
+int32_t bl_hvp_tile(const bl_problem* P, int32_t pair) { return P ? hvp_tma_tile(P, pair) : 0; }
+
+bl_status bl_set_hvp_tile(bl_problem* P, int32_t pair, int32_t side) {
+  if (!P) return fail(BL_EINVAL, "null problem");
+  return hvp_tma_force_tile(P, pair, side);
+}
+
 int32_t bl_graph_used(const bl_problem* P) { return (P && P->graph_used) ? 1 : 0; }
 
 static bl_status prof_collect(bl_problem* P) {
@@ -129,6 +136,7 @@ bl_status bl_profile_enable(bl_problem* P, int32_t enable) {
     P->prof_n[c] = 0;
   }
   BL_CUDA_TRY(cudaMemsetAsync(P->d_pix, 0, BL_KC_COUNT * sizeof(unsigned long long), P->stream));
+  BL_CUDA_TRY(cudaMemsetAsync(P->d_bytes, 0, BL_KC_COUNT * sizeof(unsigned long long), P->stream));
   BL_CUDA_TRY(cudaStreamSynchronize(P->stream));
   P->prof = enable != 0;
   return BL_OK;
@@ -144,6 +152,16 @@ bl_status bl_profile_read(bl_problem* P, int32_t cls, double* total_ms, int64_t*
   if (total_ms) *total_ms = P->prof_ms[cls];
   if (launches) *launches = P->prof_n[cls];
   if (pixels) *pixels = (int64_t)pix[cls];
+  return BL_OK;
+}
+
+bl_status bl_profile_read_bytes(bl_problem* P, int32_t cls, int64_t* bytes) {
+  if (!P || !bytes) return fail(BL_EINVAL, "null argument");
+  if (cls < 0 || cls >= BL_KC_COUNT) return fail(BL_EINVAL, "unknown kernel class");
+  BL_CUDA_TRY(cudaStreamSynchronize(P->stream));
+  unsigned long long b[BL_KC_COUNT];
+  BL_CUDA_TRY(cudaMemcpy(b, P->d_bytes, sizeof(b), cudaMemcpyDeviceToHost));
+  *bytes = (int64_t)b[cls];
   return BL_OK;
 }
 
@@ -183,7 +201,7 @@ void bl_problem_destroy(bl_problem* P) {
                   P->lx, P->lg, P->ld, P->lxt, P->lgt, P->lq, P->S, P->Yh, P->lsy, P->lyy, P->lcs, P->lcy,
                   P->lst, P->tpart, P->cpart, P->vals,
                   P->d_pix, P->d_zero, P->d_loop, P->mv_prev, P->my1, P->my2, P->mrs, P->d_opmask, P->lz_alpha, P->lz_rho, P->lz_c,
-                  P->d_tmaps, P->d_kerr};
+                  P->d_tmaps, P->d_kerr, P->d_bytes, P->d_htiles};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (P->h_flag) cudaFreeHost(P->h_flag);
@@ -379,6 +397,7 @@ bl_status bl_problem_create(const bl_pair_desc* pairs, int32_t K, const bl_reg_d
   BL_ALLOC(dalloc((void**)&P->dY3, std::max(4 * tm2, (size_t)K * kMaxHistory) * sizeof(double)));
   BL_ALLOC(dalloc((void**)&P->vals, 8 * (size_t)K * sizeof(double)));
   BL_ALLOC(dalloc((void**)&P->d_pix, BL_KC_COUNT * sizeof(unsigned long long)));
+  BL_ALLOC(dalloc((void**)&P->d_bytes, BL_KC_COUNT * sizeof(unsigned long long)));
   BL_ALLOC(dalloc((void**)&P->d_kerr, sizeof(int)));
   if (cudaMallocHost((void**)&P->h_flag, sizeof(int)) != cudaSuccess) {
     bl_problem_destroy(P);
@@ -389,6 +408,7 @@ bl_status bl_problem_create(const bl_pair_desc* pairs, int32_t K, const bl_reg_d
     return cudaMemcpyAsync(dst, src, bytes, kind, P->stream);
   };
   cudaError_t e = cudaSuccess;
+  P->pd_host = pd;
   e = e == cudaSuccess ? cpy(P->d_pairs, pd.data(), K * sizeof(PairDev), cudaMemcpyHostToDevice) : e;
   if (!hmask.empty()) e = e == cudaSuccess ? cpy(P->d_opmask, hmask.data(), n, cudaMemcpyHostToDevice) : e;
   e = e == cudaSuccess ? cpy(P->d_tiles, tiles.data(), tiles.size() * sizeof(TileDev), cudaMemcpyHostToDevice) : e;
@@ -618,19 +638,33 @@ struct RecycleHeader {
 };
 static const uint32_t kMagic = 0x424c5243u;   // "BLRC"
 
+// Stored Krylov basis of a pair (what the next bl_ritz_update reads): its columns in storage order and,
+// for a Lanczos record, the CG coefficients of the steps it holds.
+struct BasisHeader {
+  int32_t kb, lz, lzu, head, ncols, kmax;
+};
+
+static size_t basis_bytes(const bl_problem* P, int pair) {
+  const int kb = P->kb_k[pair];
+  const int ncols = P->lz_k[pair] ? std::min(kb + 1, P->KMAX) : kb;
+  size_t b = sizeof(BasisHeader) + (size_t)ncols * P->ph[pair].n * P->esz;
+  if (P->lz_k[pair]) b += (size_t)P->KMAX * (2 + P->SMAX) * sizeof(double);
+  return b;
+}
+
 bl_status bl_recycle_export(bl_problem* P, int32_t pair, void* buf, size_t* bytes) {
   if (!P || !bytes) return fail(BL_EINVAL, "null argument");
   if (pair < 0 || pair >= P->K) return fail(BL_EINVAL, "pair index out of range");
   const PairHost& ph = P->ph[pair];
   const int s = P->s_k[pair];
   const size_t vec = (size_t)s * ph.n * P->esz;
-  const size_t need = sizeof(RecycleHeader) + 3 * vec + (size_t)s * s * sizeof(double);
+  const size_t need = sizeof(RecycleHeader) + 3 * vec + (size_t)s * s * sizeof(double) + basis_bytes(P, pair);
   if (!buf) {
     *bytes = need;
     return BL_OK;
   }
   if (*bytes < need) return fail(BL_EINVAL, "checkpoint buffer too small");
-  RecycleHeader hd{kMagic, 1, P->prec, ph.h, ph.w, s, P->hz_k[pair], P->SMAX};
+  RecycleHeader hd{kMagic, 2, P->prec, ph.h, ph.w, s, P->hz_k[pair], P->SMAX};
   char* o = (char*)buf;
   memcpy(o, &hd, sizeof(hd));
   o += sizeof(hd);
@@ -644,6 +678,26 @@ bl_status bl_recycle_export(bl_problem* P, int32_t pair, void* buf, size_t* byte
   std::vector<double> ztc((size_t)P->SMAX * P->SMAX);
   BL_CUDA_TRY(cudaMemcpyAsync(ztc.data(), P->ztc + (size_t)pair * P->SMAX * P->SMAX, ztc.size() * sizeof(double),
                               cudaMemcpyDeviceToHost, P->stream));
+  // the stored basis (and Lanczos record) that the next refresh reads
+  char* ob = o + 3 * vec + (size_t)s * s * sizeof(double);
+  const int kb = P->kb_k[pair];
+  BasisHeader bh{kb, P->lz_k[pair], P->lz_u[pair], P->head_k[pair], P->lz_k[pair] ? std::min(kb + 1, P->KMAX) : kb,
+                 P->KMAX};
+  memcpy(ob, &bh, sizeof(bh));
+  char* ov = ob + sizeof(bh);
+  const size_t bvec = (size_t)bh.ncols * ph.n * P->esz;
+  if (bvec)
+    BL_CUDA_TRY(cudaMemcpyAsync(ov, (const char*)P->V + (size_t)ph.off * P->KMAX * P->esz, bvec,
+                                cudaMemcpyDeviceToHost, P->stream));
+  if (bh.lz) {
+    char* oc = ov + bvec;
+    const size_t km = (size_t)P->KMAX;
+    BL_CUDA_TRY(cudaMemcpyAsync(oc, P->lz_alpha + pair * km, km * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
+    BL_CUDA_TRY(cudaMemcpyAsync(oc + km * sizeof(double), P->lz_rho + pair * km, km * sizeof(double),
+                                cudaMemcpyDeviceToHost, P->stream));
+    BL_CUDA_TRY(cudaMemcpyAsync(oc + 2 * km * sizeof(double), P->lz_c + pair * km * P->SMAX,
+                                km * P->SMAX * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
+  }
   BL_CUDA_TRY(cudaStreamSynchronize(P->stream));
   double* zo = (double*)(o + 3 * vec);
   for (int i = 0; i < s; ++i)
@@ -659,16 +713,30 @@ bl_status bl_recycle_import(bl_problem* P, int32_t pair, const void* buf, size_t
   RecycleHeader hd;
   memcpy(&hd, buf, sizeof(hd));
   const PairHost& ph = P->ph[pair];
-  if (hd.magic != kMagic || hd.version != 1) return fail(BL_EINVAL, "not a recycle checkpoint");
+  if (hd.magic != kMagic || (hd.version != 1 && hd.version != 2)) return fail(BL_EINVAL, "not a recycle checkpoint");
   if (hd.prec != P->prec || hd.height != ph.h || hd.width != ph.w)
     return fail(BL_EINVAL, "checkpoint does not match this pair's size or precision");
   if (hd.s < 0 || hd.s > P->reg.max_recycle || hd.hasz < 0 || hd.hasz > 1)
     return fail(BL_EINVAL, "checkpoint recycle dimension out of range");
   const int s = hd.s;
   const size_t vec = (size_t)s * ph.n * P->esz;
-  const size_t need = sizeof(RecycleHeader) + 3 * vec + (size_t)s * s * sizeof(double);
-  if (bytes < need) return fail(BL_EINVAL, "checkpoint truncated");
+  const size_t need1 = sizeof(RecycleHeader) + 3 * vec + (size_t)s * s * sizeof(double);
+  if (bytes < need1) return fail(BL_EINVAL, "checkpoint truncated");
   const char* in = (const char*)buf + sizeof(hd);
+  BasisHeader bh{0, 0, 0, 0, 0, P->KMAX};
+  const char* ib = in + 3 * vec + (size_t)s * s * sizeof(double);
+  if (hd.version == 2) {
+    if (bytes < need1 + sizeof(BasisHeader)) return fail(BL_EINVAL, "checkpoint truncated");
+    memcpy(&bh, ib, sizeof(bh));
+    if (bh.kmax != P->KMAX || hd.smax != P->SMAX)
+      return fail(BL_EINVAL, "checkpoint basis needs the same max_basis and max_recycle");
+    if (bh.kb < 0 || bh.ncols < 0 || bh.ncols > P->KMAX || bh.lz < 0 || bh.lz > 1 ||
+        bh.ncols != (bh.lz ? std::min(bh.kb + 1, P->KMAX) : bh.kb))
+      return fail(BL_EINVAL, "checkpoint basis out of range");
+    size_t nb = sizeof(BasisHeader) + (size_t)bh.ncols * ph.n * P->esz;
+    if (bh.lz) nb += (size_t)P->KMAX * (2 + P->SMAX) * sizeof(double);
+    if (bytes < need1 + nb) return fail(BL_EINVAL, "checkpoint truncated");
+  }
   const size_t base = (size_t)ph.off * P->SMAX * P->esz;
   BL_CUDA_TRY(cudaMemcpyAsync((char*)P->U + base, in, vec, cudaMemcpyHostToDevice, P->stream));
   BL_CUDA_TRY(cudaMemcpyAsync((char*)P->C + base, in + vec, vec, cudaMemcpyHostToDevice, P->stream));
@@ -683,10 +751,27 @@ bl_status bl_recycle_import(bl_problem* P, int32_t pair, const void* buf, size_t
     }
   BL_CUDA_TRY(cudaMemcpyAsync(P->ztc + (size_t)pair * P->SMAX * P->SMAX, ztc.data(), ztc.size() * sizeof(double),
                               cudaMemcpyHostToDevice, P->stream));
+  if (bh.ncols) {
+    const char* iv = ib + sizeof(BasisHeader);
+    const size_t bvec = (size_t)bh.ncols * ph.n * P->esz;
+    BL_CUDA_TRY(cudaMemcpyAsync((char*)P->V + (size_t)ph.off * P->KMAX * P->esz, iv, bvec, cudaMemcpyHostToDevice,
+                                P->stream));
+    if (bh.lz) {
+      const char* ic = iv + bvec;
+      const size_t km = (size_t)P->KMAX;
+      BL_CUDA_TRY(cudaMemcpyAsync(P->lz_alpha + pair * km, ic, km * sizeof(double), cudaMemcpyHostToDevice, P->stream));
+      BL_CUDA_TRY(cudaMemcpyAsync(P->lz_rho + pair * km, ic + km * sizeof(double), km * sizeof(double),
+                                  cudaMemcpyHostToDevice, P->stream));
+      BL_CUDA_TRY(cudaMemcpyAsync(P->lz_c + pair * km * P->SMAX, ic + 2 * km * sizeof(double),
+                                  km * P->SMAX * sizeof(double), cudaMemcpyHostToDevice, P->stream));
+    }
+  }
   P->s_k[pair] = s;
   P->hz_k[pair] = hd.hasz;
-  P->kb_k[pair] = 0;
-  P->lz_k[pair] = 0;
+  P->kb_k[pair] = bh.kb;
+  P->lz_k[pair] = bh.lz;
+  P->lz_u[pair] = bh.lzu;
+  P->head_k[pair] = bh.head;
   BL_CUDA_TRY(cudaMemcpyAsync(P->d_s, P->s_k.data(), P->K * sizeof(int), cudaMemcpyHostToDevice, P->stream));
   BL_CUDA_TRY(cudaMemcpyAsync(P->d_hasz, P->hz_k.data(), P->K * sizeof(int), cudaMemcpyHostToDevice, P->stream));
   BL_CUDA_TRY(cudaStreamSynchronize(P->stream));

@@ -11,8 +11,9 @@
 //   4. Small FP64 problem on one CTA per pair:
 //        Ritz (eq. (3.1))      eigh(T), select smallest / largest / both;
 //        harmonic (eq. (3.2))  (HW~)^T HW~ rho = theta T rho via Cholesky of T;
-//        RGSV (Thm 3.1, eq. (3.4))  mu^2, V_H = eigh(T^{-1} J~^T J~ T^{-1}) (the singular values of
-//        J~ T^{-1}), X = T^{-1} V_H D_H, D_H = diag(1 / sqrt(1 + mu^2)); Z = W~ V_H diag(mu).
+//        RGSV (Thm 3.1, eq. (3.4))  mu, V_H = singular values and right singular vectors of J~ T^{-1}
+//        (Householder QR of J~ T^{-1}, then one-sided Jacobi on its triangular factor: the squared
+//        matrix is never formed), X = T^{-1} V_H D_H, D_H = diag(1 / sqrt(1 + mu^2)); Z = W~ V_H diag(mu).
 //   5. U~ = W~ Y, C~ = HW~ Y (no new Hessian actions), then C~ = C R by CholeskyQR (twice),
 //      U = U~ R^{-1}, so that C = H U and C^T C = I (Section 2.2.2); Z^T C for the estimate.
 #include <algorithm>
@@ -367,35 +368,126 @@ __global__ void k_dense_select(DenseArgs a) {
       }
     return;
   }
-  // RGSV: F = J~^T J~ (t x t) into S2, M = T^{-1} F T^{-1}
-  const double* J = a.J + (size_t)k * a.jcols * a.p;
-  for (int idx = threadIdx.x; idx < t * t; idx += blockDim.x) {
-    const int i = idx / t, j = idx - (idx / t) * t;
-    if (j < i) continue;
-    double v = 0.0;
-    for (int m = 0; m < a.p; ++m) v += J[(size_t)i * a.p + m] * J[(size_t)j * a.p + m];
-    S2[i * TM + j] = v;
-    S2[j * TM + i] = v;
+  // RGSV (Theorem 3.1): the singular values mu and right singular vectors V_H of B = J~ T^{-1},
+  // computed without forming B^T B (which would square the conditioning and lose the small mu):
+  //   B^T = T^{-1} J~^T by two triangular solves with the Cholesky factor (in place in J's storage);
+  //   B = Q R_B by Householder reflections (Q is not kept);
+  //   one-sided Jacobi on the columns of R_B: R_B V_H = [mu_1 q_1, ...], so mu_l = ||column l||.
+  double* Bt = const_cast<double*>(a.J) + (size_t)k * a.jcols * a.p;   // t x p, row j = column j of B
+  const int p = a.p;
+  dev_chol_solve(S1, t, TM, Bt, p, p);            // rows of Bt: T^{-1} J~^T
+  const int r = min(p, t);                        // rows of R_B
+  double* Rb = As;                                // R_B, column-major: column l at Rb[l * r]
+  double* Vh = Vs;                                // V_H, column-major: column l at Vh[l * t]
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ double s_alpha, s_beta;
+  for (int idx = threadIdx.x; idx < r * t; idx += blockDim.x) Rb[idx] = 0.0;
+  __syncthreads();
+  for (int j = 0; j < r; ++j) {
+    double* x = Bt + (size_t)j * p;               // column j of B
+    if (wid == 0) {
+      double ss = 0.0;
+      for (int m = j + lane; m < p; m += 32) ss += x[m] * x[m];
+      ss = warp_sum(ss);
+      if (lane == 0) {
+        const double sg = sqrt(ss), x0 = x[j];
+        const double al = x0 >= 0.0 ? -sg : sg;   // R_B[j][j]
+        s_alpha = al;
+        s_beta = sg > 0.0 ? 1.0 / (sg * (sg + fabs(x0))) : 0.0;   // 2 / v^T v with v = x - al e_j
+        x[j] = x0 - al;
+      }
+    }
+    __syncthreads();
+    const double be = s_beta;
+    if (threadIdx.x == 0) Rb[j * r + j] = s_alpha;
+    // apply (I - be v v^T) to the columns l > j; warp per column
+    for (int l = j + 1 + wid; l < t; l += nw) {
+      double* y = Bt + (size_t)l * p;
+      double d = 0.0;
+      for (int m = j + lane; m < p; m += 32) d += x[m] * y[m];
+      d = warp_sum(d) * be;
+      for (int m = j + lane; m < p; m += 32) y[m] -= d * x[m];
+      __syncwarp();
+      if (lane == 0) Rb[l * r + j] = y[j];
+    }
+    __syncthreads();
+  }
+  // one-sided Jacobi (round-robin pairs; one warp per pair): rotate columns p, q of R_B and V_H
+  // until every pair is orthogonal to 1e-12 relative, at most 12 sweeps (cyclic Jacobi converges
+  // quadratically: pairs still rotating by then sit at the rounding floor of columns whose norms
+  // differ by many orders; every sweep costs ~t^3 FP64 operations on one SM's FP64 pipe)
+  for (int idx = threadIdx.x; idx < t * t; idx += blockDim.x) Vh[idx] = (idx / t == idx % t) ? 1.0 : 0.0;
+  __shared__ int s_rot;
+  const int mm = t + (t & 1);
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < mm - 1; ++rnd) {
+      for (int i = wid; i < mm / 2; i += nw) {
+        int pp, qq;
+        if (i == 0) { pp = rnd; qq = mm - 1; }
+        else { pp = (rnd + i) % (mm - 1); qq = (rnd - i + mm - 1) % (mm - 1); }
+        if (pp > qq) { const int tt = pp; pp = qq; qq = tt; }
+        if (qq >= t) continue;
+        double* cp = Rb + pp * r;
+        double* cq = Rb + qq * r;
+        double al = 0.0, bb = 0.0, ga = 0.0;
+        for (int m = lane; m < r; m += 32) {
+          al += cp[m] * cp[m];
+          bb += cq[m] * cq[m];
+          ga += cp[m] * cq[m];
+        }
+        al = warp_sum(al);
+        bb = warp_sum(bb);
+        ga = warp_sum(ga);
+        if (!(fabs(ga) > 1e-12 * sqrt(al * bb)) || ga == 0.0) continue;
+        const double ze = (bb - al) / (2.0 * ga);
+        const double tn = (ze >= 0.0 ? 1.0 : -1.0) / (fabs(ze) + sqrt(1.0 + ze * ze));
+        const double c = 1.0 / sqrt(1.0 + tn * tn), sn = c * tn;
+        for (int m = lane; m < r; m += 32) {
+          const double u = cp[m], v = cq[m];
+          cp[m] = c * u - sn * v;
+          cq[m] = sn * u + c * v;
+        }
+        double* vp = Vh + pp * t;
+        double* vq = Vh + qq * t;
+        for (int m = lane; m < t; m += 32) {
+          const double u = vp[m], v = vq[m];
+          vp[m] = c * u - sn * v;
+          vq[m] = sn * u + c * v;
+        }
+        if (lane == 0) s_rot = 1;
+      }
+      __syncthreads();
+    }
+    const int rot = s_rot;
+    __syncthreads();
+    if (!rot) break;
+  }
+  // mu_l = ||column l of R_B||, sorted ascending (ties by index) into w / perm
+  for (int l = threadIdx.x; l < t; l += blockDim.x) {
+    double ss = 0.0;
+    for (int m = 0; m < r; ++m) ss += Rb[l * r + m] * Rb[l * r + m];
+    cs[l] = sqrt(ss);
   }
   __syncthreads();
-  dev_chol_solve(S1, t, TM, S2, t, TM);        // S2 = T^{-1} F
-  for (int idx = threadIdx.x; idx < t * t; idx += blockDim.x) {
-    const int i = idx / t, j = idx - (idx / t) * t;
-    if (i < j) { const double x = S2[i * TM + j]; S2[i * TM + j] = S2[j * TM + i]; S2[j * TM + i] = x; }
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < t; ++i) perm[i] = i;
+    for (int i = 1; i < t; ++i) {
+      const int pi = perm[i];
+      const double v = cs[pi];
+      int j = i - 1;
+      while (j >= 0 && cs[perm[j]] > v) { perm[j + 1] = perm[j]; --j; }
+      perm[j + 1] = pi;
+    }
+    for (int i = 0; i < t; ++i) w[i] = cs[perm[i]];
   }
   __syncthreads();
-  dev_chol_solve(S1, t, TM, S2, t, TM);        // S2 = T^{-1} (T^{-1} F)^T = T^{-1} F T^{-1}
-  for (int idx = threadIdx.x; idx < t * t; idx += blockDim.x) {
-    const int i = idx / t, j = idx - (idx / t) * t;
-    As[idx] = 0.5 * (S2[i * TM + j] + S2[j * TM + i]);
-  }
-  __syncthreads();
-  dev_jacobi(As, Vs, t, w, cs, perm);          // ascending mu^2, V_H
-  // V_H,sel into Y2 (scaled by mu later), X_sel = T^{-1} V_H,sel D_H into Y
+  // V_H,sel into Y2 (scaled by mu below), X_sel = T^{-1} V_H,sel D_H into Y
   for (int idx = threadIdx.x; idx < t * s; idx += blockDim.x) {
     const int i = idx / s, j = idx - (idx / s) * s;
     const int e = sel_index(t, s, a.size, j);
-    const double vh = Vs[i * t + perm[e]];
+    const double vh = Vh[perm[e] * t + i];
     Y2[i * TM + j] = vh;
     Y[i * TM + j] = vh;
   }
@@ -404,7 +496,7 @@ __global__ void k_dense_select(DenseArgs a) {
   for (int idx = threadIdx.x; idx < t * s; idx += blockDim.x) {
     const int i = idx / s, j = idx - (idx / s) * s;
     const int e = sel_index(t, s, a.size, j);
-    const double mu = sqrt(fmax(w[e], 0.0));
+    const double mu = w[e];
     const double dh = 1.0 / sqrt(1.0 + mu * mu);
     const double x = Y[i * TM + j] * dh;
     const double vh = Y2[i * TM + j];

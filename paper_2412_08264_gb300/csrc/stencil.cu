@@ -417,13 +417,16 @@ template <typename T, int F>
 __global__ void __launch_bounds__(kStencilThreads, sizeof(T) == 4 ? 2 : 1)
 k_foe_jw(const PairDev* pairs, const TileDev* tiles, int n_tiles, const T* win, int mult,
          const int* cols, const T* xhat, const T* fu, const T* taps, const double* ealpha, int N,
-         T eps, int phi, long long n_tot, const int* mask, double* tpart, int p, unsigned long long* pix) {
+         T eps, int phi, long long n_tot, const int* mask, double* tpart, int p, unsigned long long* pix,
+         int colfast) {
   constexpr int R = F / 2, TILE = jw_tile_out<T>(F), RS = TILE + 2 * R;   // staged region side
   constexpr int RP = jw_pitch<T>(RS);                                 // its row pitch
   constexpr int NB = TILE / 4, FF = F * F;
-  const TileDev tl = tiles[blockIdx.x];
+  // colfast: grid x runs over the columns of one tile, so its x^ and field tiles are read from L2
+  const int ti = colfast ? blockIdx.y : blockIdx.x;
+  const TileDev tl = tiles[ti];
   const PairDev pr = pairs[tl.pair];
-  const int col = blockIdx.y;
+  const int col = colfast ? blockIdx.x : blockIdx.y;
   if (mask && !mask[tl.pair]) return;
   if (mult && col >= cols[tl.pair]) return;
   if (pix && threadIdx.x == 0)
@@ -446,7 +449,7 @@ k_foe_jw(const PairDev* pairs, const TileDev* tiles, int n_tiles, const T* win, 
   __syncthreads();
   const bool owner = tid < NB * NB;
   const int oby = owner ? tid / NB : 0, obx = owner ? tid - (tid / NB) * NB : 0;
-  double* outp = tpart + ((size_t)col * n_tiles + blockIdx.x) * p;
+  double* outp = tpart + ((size_t)col * n_tiles + ti) * p;
   // u_j of this thread's 16 pixels is prefetched one filter ahead (cp.async, per-thread slots)
   auto prefetch = [&](int jf, int buf) {
 #pragma unroll
@@ -827,6 +830,8 @@ bl_status launch_hvp(bl_problem* P, const void* in, void* out, int mult, int col
                      const int* dots_s, const int* dots_hz) {
   if (P->reg.kind == BL_REG_TV) {
     if (dots_s) return fail(BL_EINVAL, "fused dots are only available for FoE problems");
+    const int slot = hvp_tma_slot(P, in, mult);
+    if (slot >= 0) return launch_hvp_tma(P, slot, in, out, mult, cols, mask);
     return P->prec == BL_FP32 ? hvp_tv<float>(P, in, out, mult, cols, mask)
                               : hvp_tv<double>(P, in, out, mult, cols, mask);
   }
@@ -856,6 +861,15 @@ static bl_status grad_impl(bl_problem* P, const void* x, void* grad, const int* 
       if (st != BL_OK) return st;
     }
     return BL_OK;
+  }
+  if (sizeof(T) == 4) {
+    const int slot = hvp_tma_grad_slot(P, x);
+    if (slot >= 0) {
+      bl_status st = ensure_tpart(P, (size_t)P->n_htiles * 3);
+      if (st != BL_OK) return st;
+      if ((st = launch_grad_tma(P, slot, grad, mask, P->tpart)) != BL_OK) return st;
+      return values ? reduce_units(P, P->tpart, 3, 1, kUnitHTiles, mask, nullptr, values) : BL_OK;
+    }
   }
   StencilArgs<T> a{};
   a.pairs = P->d_pairs;
@@ -961,7 +975,8 @@ static bl_status jw_impl(bl_problem* P, const void* in, int mult, int cols, cons
   bl_status st = ensure_tpart(P, (size_t)P->n_jtiles * ncol * P->p);
   if (st != BL_OK) return st;
   const T* taps = P->prec == BL_FP32 ? (const T*)(const void*)P->taps_f : (const T*)(const void*)P->taps_d;
-  dim3 grid(P->n_jtiles, ncol);
+  const int colfast = (ncol > 1 && P->n_jtiles <= 65535) ? 1 : 0;
+  const dim3 grid = colfast ? dim3(ncol, P->n_jtiles) : dim3(P->n_jtiles, ncol);
   ProfScope ps(P, BL_KC_JW);
   unsigned long long* pixc = pix_counter(P, BL_KC_JW);
 #define BL_JW_CASE(FF)                                                                            \
@@ -975,7 +990,7 @@ static bl_status jw_impl(bl_problem* P, const void* in, int mult, int cols, cons
     k_foe_jw<T, FF><<<grid, kStencilThreads, sm, P->stream>>>(                                    \
         P->d_pairs, P->d_jtiles, P->n_jtiles, (const T*)in, mult, P->d_cols, (const T*)P->xhat,   \
         (const T*)P->fu, taps, P->ealpha, P->N, (T)P->reg.phi_eps, P->reg.phi, P->n_tot, mask,    \
-        P->tpart, P->p, pixc);                                                                    \
+        P->tpart, P->p, pixc, colfast);                                                           \
     break;                                                                                        \
   }
   switch (P->F) {

@@ -34,6 +34,7 @@ ProfScope::~ProfScope() {
 }
 
 unsigned long long* pix_counter(bl_problem* P, int cls) { return P->prof ? P->d_pix + cls : nullptr; }
+unsigned long long* bytes_counter(bl_problem* P, int cls) { return P->prof ? P->d_bytes + cls : nullptr; }
 
 bl_status check_kernel_error(bl_problem* P) {
   int code = 0;
@@ -132,8 +133,8 @@ __global__ void k_reduce_units(const PairDev* pairs, const double* part, int n_u
   if (mask && !mask[k]) return;
   if (colcnt && col >= colcnt[k]) return;
   const PairDev pr = pairs[k];
-  const int beg = units == kUnitTiles ? pr.tbeg : units == kUnitJwTiles ? pr.jtbeg : pr.cbeg;
-  const int end = units == kUnitTiles ? pr.tend : units == kUnitJwTiles ? pr.jtend : pr.cend;
+  const int beg = units == kUnitTiles ? pr.tbeg : units == kUnitJwTiles ? pr.jtbeg : units == kUnitHTiles ? pr.htbeg : pr.cbeg;
+  const int end = units == kUnitTiles ? pr.tend : units == kUnitJwTiles ? pr.jtend : units == kUnitHTiles ? pr.htend : pr.cend;
   for (int m = threadIdx.x; m < ncomp; m += blockDim.x) {
     double s = 0.0;
     for (int u = beg; u < end; ++u) s += part[((size_t)col * n_units + u) * ncomp + m];
@@ -143,7 +144,10 @@ __global__ void k_reduce_units(const PairDev* pairs, const double* part, int n_u
 
 bl_status reduce_units(bl_problem* P, const double* part, int ncomp, int cols, int units, const int* mask,
                        const int* colcnt, double* out) {
-  const int n_units = units == kUnitTiles ? P->n_tiles : units == kUnitJwTiles ? P->n_jtiles : P->n_chunks;
+  const int n_units = units == kUnitTiles    ? P->n_tiles
+                      : units == kUnitJwTiles ? P->n_jtiles
+                      : units == kUnitHTiles  ? P->n_htiles
+                                              : P->n_chunks;
   k_reduce_units<<<dim3(P->K, cols), 128, 0, P->stream>>>(P->d_pairs, part, n_units, ncomp, cols, units, mask,
                                                           colcnt, out);
   BL_LAUNCH_CHECK(P);
