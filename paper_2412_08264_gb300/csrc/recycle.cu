@@ -371,27 +371,70 @@ __global__ void k_dense_select(DenseArgs a) {
   // RGSV (Theorem 3.1): the singular values mu and right singular vectors V_H of B = J~ T^{-1},
   // computed without forming B^T B (which would square the conditioning and lose the small mu):
   //   B^T = T^{-1} J~^T by two triangular solves with the Cholesky factor (in place in J's storage);
-  //   B = Q R_B by Householder reflections (Q is not kept);
-  //   one-sided Jacobi on the columns of R_B: R_B V_H = [mu_1 q_1, ...], so mu_l = ||column l||.
+  //   p >= t: B P = Q R by Householder QR with column pivoting (largest remaining column first, Q
+  //     not kept), then one-sided Jacobi on the columns of M = R^T: M W = [mu_1 u_1, ...] with
+  //     R = W diag(mu) U^T, so V_H = P U, u_l = (column l of M W) / mu_l.  The pivoted factor's rows
+  //     are graded, which is what makes Jacobi on R^T converge in a few sweeps (Drmac and Veselic's
+  //     preconditioned one-sided Jacobi) where Jacobi on R itself first spends ~10 sweeps sorting;
+  //   p < t (rank <= p, the other t - p values are mu = 0): Householder QR without pivoting, then
+  //     one-sided Jacobi on the columns of R (p long) accumulating V_H: R V_H = [mu_1 q_1, ...].
   double* Bt = const_cast<double*>(a.J) + (size_t)k * a.jcols * a.p;   // t x p, row j = column j of B
   const int p = a.p;
   dev_chol_solve(S1, t, TM, Bt, p, p);            // rows of Bt: T^{-1} J~^T
-  const int r = min(p, t);                        // rows of R_B
-  double* Rb = As;                                // R_B, column-major: column l at Rb[l * r]
+  const bool tall = p >= t;
+  const int r = min(p, t);                        // rows of R
+  // tall: Rb holds M = R^T column-major (column i = row i of R, t long, at Rb[i * t]);
+  // otherwise Rb holds R column-major (column l, r long, at Rb[l * r])
+  double* Rb = As;
   double* Vh = Vs;                                // V_H, column-major: column l at Vh[l * t]
+  double* nrm = cs + TM;                          // squared norms of the unreduced parts of the columns
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   __shared__ double s_alpha, s_beta;
+  __shared__ int s_piv;
   for (int idx = threadIdx.x; idx < r * t; idx += blockDim.x) Rb[idx] = 0.0;
+  for (int l = threadIdx.x; l < t; l += blockDim.x) perm[l] = l;   // P: column l of B P is column perm[l] of B
+  if (tall)
+    for (int l = wid; l < t; l += nw) {
+      const double* y = Bt + (size_t)l * p;
+      double ss = 0.0;
+      for (int m = lane; m < p; m += 32) ss += y[m] * y[m];
+      ss = warp_sum(ss);
+      if (lane == 0) nrm[l] = ss;
+    }
   __syncthreads();
   for (int j = 0; j < r; ++j) {
-    double* x = Bt + (size_t)j * p;               // column j of B
+    if (tall) {
+      // pivot: the remaining column with the largest unreduced norm (ties to the lowest index)
+      if (threadIdx.x == 0) {
+        int best = j;
+        for (int l = j + 1; l < t; ++l)
+          if (nrm[l] > nrm[best]) best = l;
+        s_piv = best;
+      }
+      __syncthreads();
+      const int q = s_piv;
+      if (q != j) {
+        double* xj = Bt + (size_t)j * p;
+        double* xq = Bt + (size_t)q * p;
+        for (int m = threadIdx.x; m < p; m += blockDim.x) { const double u = xj[m]; xj[m] = xq[m]; xq[m] = u; }
+        for (int i = threadIdx.x; i < j; i += blockDim.x) {   // rows 0..j-1 of R already hold these columns
+          const double u = Rb[i * t + j]; Rb[i * t + j] = Rb[i * t + q]; Rb[i * t + q] = u;
+        }
+        if (threadIdx.x == 0) {
+          const double u = nrm[j]; nrm[j] = nrm[q]; nrm[q] = u;
+          const int pi = perm[j]; perm[j] = perm[q]; perm[q] = pi;
+        }
+      }
+      __syncthreads();
+    }
+    double* x = Bt + (size_t)j * p;               // column j of B (P)
     if (wid == 0) {
       double ss = 0.0;
       for (int m = j + lane; m < p; m += 32) ss += x[m] * x[m];
       ss = warp_sum(ss);
       if (lane == 0) {
         const double sg = sqrt(ss), x0 = x[j];
-        const double al = x0 >= 0.0 ? -sg : sg;   // R_B[j][j]
+        const double al = x0 >= 0.0 ? -sg : sg;   // R[j][j]
         s_alpha = al;
         s_beta = sg > 0.0 ? 1.0 / (sg * (sg + fabs(x0))) : 0.0;   // 2 / v^T v with v = x - al e_j
         x[j] = x0 - al;
@@ -399,27 +442,39 @@ __global__ void k_dense_select(DenseArgs a) {
     }
     __syncthreads();
     const double be = s_beta;
-    if (threadIdx.x == 0) Rb[j * r + j] = s_alpha;
-    // apply (I - be v v^T) to the columns l > j; warp per column
+    if (threadIdx.x == 0) Rb[tall ? j * t + j : j * r + j] = s_alpha;
+    // apply (I - be v v^T) to the columns l > j; warp per column; the unreduced norm is recomputed
     for (int l = j + 1 + wid; l < t; l += nw) {
       double* y = Bt + (size_t)l * p;
       double d = 0.0;
       for (int m = j + lane; m < p; m += 32) d += x[m] * y[m];
       d = warp_sum(d) * be;
-      for (int m = j + lane; m < p; m += 32) y[m] -= d * x[m];
+      double ss = 0.0;
+      for (int m = j + lane; m < p; m += 32) {
+        const double v = y[m] - d * x[m];
+        y[m] = v;
+        if (m > j) ss += v * v;
+      }
+      ss = warp_sum(ss);
       __syncwarp();
-      if (lane == 0) Rb[l * r + j] = y[j];
+      if (lane == 0) {
+        nrm[l] = ss;
+        if (tall) Rb[j * t + l] = y[j];
+        else Rb[l * r + j] = y[j];
+      }
     }
     __syncthreads();
   }
-  // one-sided Jacobi (round-robin pairs; one warp per pair): rotate columns p, q of R_B and V_H
-  // until every pair is orthogonal to 1e-12 relative, at most 12 sweeps (cyclic Jacobi converges
-  // quadratically: pairs still rotating by then sit at the rounding floor of columns whose norms
-  // differ by many orders; every sweep costs ~t^3 FP64 operations on one SM's FP64 pipe)
-  for (int idx = threadIdx.x; idx < t * t; idx += blockDim.x) Vh[idx] = (idx / t == idx % t) ? 1.0 : 0.0;
+  // one-sided Jacobi (round-robin pairs; one warp per pair) on the n columns (each len long) of Rb,
+  // rotating V_H alongside unless tall: until every pair is orthogonal to 1e-12 relative, at most
+  // 30 sweeps (pairs still rotating then sit at the rounding floor of columns whose norms differ by
+  // many orders)
+  const int n = tall ? r : t, len = tall ? t : r;
+  if (!tall)
+    for (int idx = threadIdx.x; idx < t * t; idx += blockDim.x) Vh[idx] = (idx / t == idx % t) ? 1.0 : 0.0;
   __shared__ int s_rot;
-  const int mm = t + (t & 1);
-  for (int sweep = 0; sweep < 12; ++sweep) {
+  const int mm = n + (n & 1);
+  for (int sweep = 0; sweep < 30; ++sweep) {
     if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
     for (int rnd = 0; rnd < mm - 1; ++rnd) {
@@ -428,11 +483,11 @@ __global__ void k_dense_select(DenseArgs a) {
         if (i == 0) { pp = rnd; qq = mm - 1; }
         else { pp = (rnd + i) % (mm - 1); qq = (rnd - i + mm - 1) % (mm - 1); }
         if (pp > qq) { const int tt = pp; pp = qq; qq = tt; }
-        if (qq >= t) continue;
-        double* cp = Rb + pp * r;
-        double* cq = Rb + qq * r;
+        if (qq >= n) continue;
+        double* cp = Rb + pp * len;
+        double* cq = Rb + qq * len;
         double al = 0.0, bb = 0.0, ga = 0.0;
-        for (int m = lane; m < r; m += 32) {
+        for (int m = lane; m < len; m += 32) {
           al += cp[m] * cp[m];
           bb += cq[m] * cq[m];
           ga += cp[m] * cq[m];
@@ -444,17 +499,19 @@ __global__ void k_dense_select(DenseArgs a) {
         const double ze = (bb - al) / (2.0 * ga);
         const double tn = (ze >= 0.0 ? 1.0 : -1.0) / (fabs(ze) + sqrt(1.0 + ze * ze));
         const double c = 1.0 / sqrt(1.0 + tn * tn), sn = c * tn;
-        for (int m = lane; m < r; m += 32) {
+        for (int m = lane; m < len; m += 32) {
           const double u = cp[m], v = cq[m];
           cp[m] = c * u - sn * v;
           cq[m] = sn * u + c * v;
         }
-        double* vp = Vh + pp * t;
-        double* vq = Vh + qq * t;
-        for (int m = lane; m < t; m += 32) {
-          const double u = vp[m], v = vq[m];
-          vp[m] = c * u - sn * v;
-          vq[m] = sn * u + c * v;
+        if (!tall) {
+          double* vp = Vh + pp * t;
+          double* vq = Vh + qq * t;
+          for (int m = lane; m < t; m += 32) {
+            const double u = vp[m], v = vq[m];
+            vp[m] = c * u - sn * v;
+            vq[m] = sn * u + c * v;
+          }
         }
         if (lane == 0) s_rot = 1;
       }
@@ -464,13 +521,22 @@ __global__ void k_dense_select(DenseArgs a) {
     __syncthreads();
     if (!rot) break;
   }
-  // mu_l = ||column l of R_B||, sorted ascending (ties by index) into w / perm
-  for (int l = threadIdx.x; l < t; l += blockDim.x) {
+  // mu_l = ||column l of Rb||; tall: V_H column l = P (column l / mu_l) (e_{P l} for mu_l = 0, which
+  // needs J~ rank-deficient with p >= t)
+  for (int l = threadIdx.x; l < n; l += blockDim.x) {
     double ss = 0.0;
-    for (int m = 0; m < r; ++m) ss += Rb[l * r + m] * Rb[l * r + m];
+    for (int m = 0; m < len; ++m) ss += Rb[l * len + m] * Rb[l * len + m];
     cs[l] = sqrt(ss);
   }
   __syncthreads();
+  if (tall)
+    for (int idx = threadIdx.x; idx < t * t; idx += blockDim.x) {
+      const int l = idx / t, m = idx - (idx / t) * t;
+      const double mu = cs[l];
+      Vh[l * t + perm[m]] = mu > 0.0 ? Rb[l * t + m] / mu : (m == l ? 1.0 : 0.0);
+    }
+  __syncthreads();
+  // sorted ascending (ties by index) into w / perm
   if (threadIdx.x == 0) {
     for (int i = 0; i < t; ++i) perm[i] = i;
     for (int i = 1; i < t; ++i) {

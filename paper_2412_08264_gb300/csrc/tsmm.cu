@@ -357,6 +357,14 @@ bl_status ts_gemm(bl_problem* P, const void* A, int multA, const int* colsA, int
                   int mult1, const int* cols1, int cmax1, const double* M2, void* O2, int mult2, const int* cols2,
                   int cmax2, const int* mask) {
   const int TM = P->TM;
+  if (P->prec == BL_FP32 && O2 && (cmax1 + cmax2 + 7) / 8 > 12) {
+    // two products too wide for one pass (more than 96 output columns together): the second first,
+    // since the first may overwrite A in place
+    bl_status st = ts_gemm(P, A, multA, colsA, cmaxA, M2, O2, mult2, cols2, cmax2, nullptr, nullptr, 0, nullptr, 0,
+                           mask);
+    if (st != BL_OK) return st;
+    return ts_gemm(P, A, multA, colsA, cmaxA, M1, O1, mult1, cols1, cmax1, nullptr, nullptr, 0, nullptr, 0, mask);
+  }
   ProfScope ps(P, BL_KC_GEMM);
   if (P->prec == BL_FP32) {
     const int ngrp = std::max(1, (cmax1 + (O2 ? cmax2 : 0) + 7) / 8);

@@ -103,13 +103,11 @@ def test_autograd_backward_matches_checker_and_fd_fp64():
     assert rel(grad, ref) < 1e-6, rel(grad, ref)
     # central finite differences of L along random directions (lower solves on the GPU, FP64)
     rng = np.random.default_rng(0)
-    # central differences through L-BFGS lower solves stopped at a relative gradient of 1e-8: their
-    # stopping error enters divided by 2h (noise ~1e-5 at h = 1e-4; at 1e-9 the FP64 Armijo test stops
-    # resolving decreases and the solves spend their halvings), while h = 1e-3 already shows O(h^2)
-    # truncation of ~1e-4 on this loss, so the difference is held to 1e-4; the backward pass itself is
-    # held to 1e-6 against the checker's hypergradient above
+    # central differences through L-BFGS lower solves stopped at a relative gradient of 1e-9: their
+    # stopping error enters divided by 2h (noise ~1e-6 at h = 1e-4), while h = 1e-3 already shows
+    # O(h^2) truncation of ~1e-4 on this loss, so the difference is held to 1e-4; the backward pass
+    # itself is held to 1e-6 against the checker's hypergradient above
     h = 1e-4
-    eng.lower_gtol = 1e-8
     for _ in range(3):
         d = rng.standard_normal(P.p)
         d /= np.linalg.norm(d)
