@@ -269,46 +269,68 @@ __global__ void k_dots(KrylovArgs a, const T* p, const T* q, const T* C, const T
 }
 
 // The same partials for FP32 problems whose images are multiples of 4 pixels (16-byte aligned column
-// starts): one warp per component streams its column of the chunk with 128-bit loads, eight in
-// flight per lane, against q (re-read from L1), so no barrier separates the components.
-__global__ void k_dots_v4(KrylovArgs a, const float* p, const float* q, const float* C, const float* Z) {
+// starts): every thread keeps its four 128-bit blocks of q in registers (a chunk is 4,096 pixels =
+// 1,024 blocks) and streams the matching blocks of the components, eight components per group with
+// all their loads in flight, into compensated FP32 sums; one barrier per group combines the warps
+// in FP64.  q is read once, and no warp idles while another finishes a component.
+__global__ void __launch_bounds__(kChunkThreads) k_dots_v4(KrylovArgs a, const float* p, const float* q,
+                                                           const float* C, const float* Z) {
+  constexpr int NW = kChunkThreads / 32, GC = 8, PB = kChunk / 4 / kChunkThreads;
+  static_assert(PB * 4 * kChunkThreads == kChunk, "a chunk is PB 128-bit blocks per thread");
+  __shared__ double red[NW][GC];
   const ChunkDev ch = a.chunks[blockIdx.x];
   if (!a.st[ch.pair].active) return;
   const PairDev pr = a.pairs[ch.pair];
   const int s = a.s_k[ch.pair];
   const int nz = a.hasz[ch.pair] ? s : 0;
-  const int ncomp = 1 + 2 * a.SMAX;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int ncomp = 1 + 2 * a.SMAX, nc = 1 + s + nz;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (a.nbytes && threadIdx.x == 0) atomicAdd(a.nbytes, (unsigned long long)ch.len * 4ull * (2 + s + nz));
   const int nv = ch.len >> 2;                                  // chunk lengths are multiples of 4
   const float4* q4 = reinterpret_cast<const float4*>(q + pr.off + ch.start);
-  for (int comp = wid; comp < 1 + s + nz; comp += nw) {
-    const float* src = comp == 0 ? p + pr.off
-                                 : (comp <= s ? C + pr.off * a.SMAX + (long long)(comp - 1) * pr.n
-                                              : Z + pr.off * a.SMAX + (long long)(comp - 1 - s) * pr.n);
-    const float4* s4 = reinterpret_cast<const float4*>(src + ch.start);
-    Accum<float> acc;
-    for (int i0 = 0; i0 < nv; i0 += 32 * 8) {
-      float4 u[8], v[8];
+  float4 qv[PB];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int i = i0 + j * 32 + lane;
-        u[j] = i < nv ? s4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-        v[j] = i < nv ? q4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
+  for (int m = 0; m < PB; ++m) {
+    const int i = threadIdx.x + m * kChunkThreads;
+    qv[m] = i < nv ? q4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  for (int g0 = 0; g0 < nc; g0 += GC) {
+    Accum<float> acc[GC];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        acc.add(u[j].x * v[j].x);
-        acc.add(u[j].y * v[j].y);
-        acc.add(u[j].z * v[j].z);
-        acc.add(u[j].w * v[j].w);
+    for (int c = 0; c < GC; ++c) {
+      const int comp = g0 + c;
+      if (comp >= nc) break;
+      const float* src = comp == 0 ? p + pr.off
+                                   : (comp <= s ? C + pr.off * a.SMAX + (long long)(comp - 1) * pr.n
+                                                : Z + pr.off * a.SMAX + (long long)(comp - 1 - s) * pr.n);
+      const float4* s4 = reinterpret_cast<const float4*>(src + ch.start);
+#pragma unroll
+      for (int m = 0; m < PB; ++m) {
+        const int i = threadIdx.x + m * kChunkThreads;
+        if (i < nv) {
+          const float4 u = s4[i];
+          acc[c].add(u.x * qv[m].x);
+          acc[c].add(u.y * qv[m].y);
+          acc[c].add(u.z * qv[m].z);
+          acc[c].add(u.w * qv[m].w);
+        }
       }
     }
-    const double tot = warp_total(acc);
-    if (lane == 0) {
+#pragma unroll
+    for (int c = 0; c < GC; ++c) {
+      const double t = warp_total(acc[c]);
+      if (lane == 0) red[wid][c] = t;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < GC && g0 + (int)threadIdx.x < nc) {
+      double tot = 0.0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) tot += red[w][threadIdx.x];
+      const int comp = g0 + threadIdx.x;
       const int slot = comp <= s ? comp : comp - s + a.SMAX;
       a.cpart[(size_t)blockIdx.x * ncomp + slot] = tot;
     }
+    __syncthreads();
   }
 }
 
@@ -987,7 +1009,7 @@ static bl_status solve_impl(bl_problem* P, const int* mask_host, const bl_krylov
   int* d_itmask = P->d_active + K; // per-pair active copy for the stencil mask
   const int store = P->KMAX > 0 ? (o->store_basis == BL_STORE_LANCZOS ? 2 : (o->store_basis ? 1 : 0)) : 0;
   const int nsc = o->stop == BL_STOP_NSC ? 1 : 0;
-  // dot products of the unfused path: one warp per component for aligned FP32 problems
+  // dot products of the unfused path: all components of a chunk per CTA for aligned FP32 problems
   auto launch_dots = [&](const KrylovArgs& a0) -> bl_status {
     if (sizeof(T) == 4 && P->vec4)
       k_dots_v4<<<P->n_chunks, kChunkThreads, 0, P->stream>>>(a0, (const float*)(const void*)p,
