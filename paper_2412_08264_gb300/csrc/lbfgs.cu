@@ -80,36 +80,44 @@ __global__ void k_lb_dots(LbArgs a, const T* g, const T* Sm, const T* Ym, double
 // Per pair: update S^T Y and Y^T Y for the newest pair, solve with R (FP64) and write the direction
 // coefficients by slot: d = -gamma g + sum_i cs_i s_i + cy_i y_i.
 __global__ void k_lb_compact(LbArgs a, const double* part) {
-  __shared__ double v[4 * (kMaxHistory + 1)];
+  constexpr int M = kMaxHistory;
+  __shared__ double v[4 * (M + 1)];
+  __shared__ double R[M][M], YY[M][M];   // by age: R = upper triangle of S^T Y, YY = Y^T Y
+  __shared__ double u[M], w[M], top[M];
+  __shared__ int sl[M];
   const int k = blockIdx.x;
   const LbfgsState S = a.st[k];
   if (!S.active || S.phase != kLbDir) return;
   const PairDev pr = a.pairs[k];
   const int RS = a.MH + 1, c = S.hist_count;
-  for (int q = threadIdx.x; q < 4 * c; q += blockDim.x) {
-    double t = 0.0;
-    for (int u = pr.cbeg; u < pr.cend; ++u) t += part[(size_t)u * 4 * RS + q];
-    v[q] = t;
-  }
-  __syncthreads();
-  if (threadIdx.x != 0) return;
   double* sy = a.sy + (size_t)k * RS * RS;    // sy[i * RS + j] = s_i^T y_j (slots)
   double* yy = a.yy + (size_t)k * RS * RS;
   double* cs = a.cs + (size_t)k * RS;
   double* cy = a.cy + (size_t)k * RS;
-  for (int j = 0; j < RS; ++j) cs[j] = cy[j] = 0.0;
-  if (c == 0) return;
-  const int nw = lb_age_slot(S, c - 1, RS);
-  for (int i = 0; i < c; ++i) {
-    const int sl = lb_age_slot(S, i, RS);
-    sy[sl * RS + nw] = v[4 * i + 2];
-    yy[sl * RS + nw] = v[4 * i + 3];
-    yy[nw * RS + sl] = v[4 * i + 3];
+  for (int q = threadIdx.x; q < 4 * c; q += blockDim.x) {
+    double t = 0.0;
+    for (int un = pr.cbeg; un < pr.cend; ++un) t += part[(size_t)un * 4 * RS + q];
+    v[q] = t;
   }
-  double R[kMaxHistory][kMaxHistory], u[kMaxHistory], w[kMaxHistory], top[kMaxHistory];
-  for (int i = 0; i < c; ++i)
-    for (int j = 0; j < c; ++j)
-      R[i][j] = (j >= i) ? sy[lb_age_slot(S, i, RS) * RS + lb_age_slot(S, j, RS)] : 0.0;
+  for (int j = threadIdx.x; j < RS; j += blockDim.x) cs[j] = cy[j] = 0.0;
+  for (int i = threadIdx.x; i < c; i += blockDim.x) sl[i] = lb_age_slot(S, i, RS);
+  __syncthreads();
+  if (c == 0) return;
+  // the newest pair's column of S^T Y and row / column of Y^T Y (slots, kept across iterations)
+  const int nw = sl[c - 1];
+  for (int i = threadIdx.x; i < c; i += blockDim.x) {
+    sy[sl[i] * RS + nw] = v[4 * i + 2];
+    yy[sl[i] * RS + nw] = v[4 * i + 3];
+    yy[nw * RS + sl[i]] = v[4 * i + 3];
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < c * c; idx += blockDim.x) {
+    const int i = idx / c, j = idx - (idx / c) * c;
+    R[i][j] = (j >= i) ? sy[sl[i] * RS + sl[j]] : 0.0;
+    YY[i][j] = yy[sl[i] * RS + sl[j]];
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
   const double gam = S.gamma;
   // u = R^{-1} (S^T g)
   for (int i = c - 1; i >= 0; --i) {
@@ -120,7 +128,7 @@ __global__ void k_lb_compact(LbArgs a, const double* part) {
   // w = (D + gamma Y^T Y) u - gamma Y^T g
   for (int i = 0; i < c; ++i) {
     double t = R[i][i] * u[i] - gam * v[4 * i + 1];
-    for (int j = 0; j < c; ++j) t += gam * yy[lb_age_slot(S, i, RS) * RS + lb_age_slot(S, j, RS)] * u[j];
+    for (int j = 0; j < c; ++j) t += gam * YY[i][j] * u[j];
     w[i] = t;
   }
   // top = R^{-T} w
@@ -130,9 +138,8 @@ __global__ void k_lb_compact(LbArgs a, const double* part) {
     top[i] = t / R[i][i];
   }
   for (int i = 0; i < c; ++i) {
-    const int sl = lb_age_slot(S, i, RS);
-    cs[sl] = -top[i];
-    cy[sl] = gam * u[i];
+    cs[sl[i]] = -top[i];
+    cy[sl[i]] = gam * u[i];
   }
 }
 
@@ -175,10 +182,12 @@ __global__ void k_lb_dir(LbArgs a, T* d, const T* g, const T* Sm, const T* Ym, d
 __global__ void k_lb_gtd(LbArgs a, const double* part) {
   const int k = blockIdx.x;
   LbfgsState& S = a.st[k];
-  if (!S.active || S.phase != kLbDir || threadIdx.x != 0) return;
+  if (!S.active || S.phase != kLbDir) return;
   const PairDev pr = a.pairs[k];
   double sum = 0.0;
-  for (int u = pr.cbeg; u < pr.cend; ++u) sum += part[u];
+  for (int u = pr.cbeg + (int)threadIdx.x; u < pr.cend; u += 32) sum += part[u];
+  sum = warp_sum(sum);
+  if (threadIdx.x != 0) return;
   S.gtd = sum;
   S.accepted = (sum >= 0.0) ? -1 : 0;   // -1: not a descent direction
 }
@@ -204,10 +213,12 @@ __global__ void k_lb_restart(LbArgs a, T* d, const T* g) {
 __global__ void k_lb_restart_fix(LbArgs a) {
   const int k = blockIdx.x;
   LbfgsState& S = a.st[k];
-  if (!S.active || S.phase != kLbDir || threadIdx.x != 0 || S.accepted != -1) return;
+  if (!S.active || S.phase != kLbDir || S.accepted != -1) return;
   const PairDev pr = a.pairs[k];
   double sum = 0.0;
-  for (int u = pr.cbeg; u < pr.cend; ++u) sum += a.cpart[u];
+  for (int u = pr.cbeg + (int)threadIdx.x; u < pr.cend; u += 32) sum += a.cpart[u];
+  sum = warp_sum(sum);
+  if (threadIdx.x != 0) return;
   S.gtd = sum;
   S.hist_count = 0;
   S.accepted = 0;
@@ -296,16 +307,202 @@ __global__ void k_lb_accept(LbArgs a, T* x, T* g, const T* xt, const T* gt, T* S
   }
 }
 
+// 128-bit versions of the four vector passes for FP32 problems whose images are multiples of 4
+// pixels (every column start 16-byte aligned; a chunk is kChunk pixels, PB float4 per thread).
+// Each thread keeps its blocks of g (and y_new) in registers and streams the history columns.
+constexpr int kLbPB = kChunk / 4 / kChunkThreads;
+static_assert(kLbPB * 4 * kChunkThreads == kChunk, "PB 128-bit blocks per thread");
+
+__device__ __forceinline__ void add4(Accum<float>& acc, float4 u, float4 v) {
+  acc.add(u.x * v.x);
+  acc.add(u.y * v.y);
+  acc.add(u.z * v.z);
+  acc.add(u.w * v.w);
+}
+
+__global__ void __launch_bounds__(kChunkThreads) k_lb_dots_v4(LbArgs a, const float* g, const float* Sm,
+                                                              const float* Ym, double* part) {
+  __shared__ double red[kChunkThreads / 32][4 * (kMaxHistory + 1)];
+  const ChunkDev ch = a.chunks[blockIdx.x];
+  const LbfgsState S = a.st[ch.pair];
+  if (!S.active || S.phase != kLbDir || S.hist_count == 0) return;
+  const PairDev pr = a.pairs[ch.pair];
+  const int RS = a.MH + 1, c = S.hist_count, nv = ch.len >> 2;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const float4* g4 = reinterpret_cast<const float4*>(g + pr.off + ch.start);
+  const float4* yn4 =
+      reinterpret_cast<const float4*>(Ym + pr.off * RS + (long long)lb_age_slot(S, c - 1, RS) * pr.n + ch.start);
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 gv[kLbPB], ynv[kLbPB];
+#pragma unroll
+  for (int m = 0; m < kLbPB; ++m) {
+    const int i = threadIdx.x + m * kChunkThreads;
+    gv[m] = i < nv ? g4[i] : z4;
+    ynv[m] = i < nv ? yn4[i] : z4;
+  }
+  for (int h = 0; h < c; ++h) {
+    const long long col = pr.off * RS + (long long)lb_age_slot(S, h, RS) * pr.n + ch.start;
+    const float4* s4 = reinterpret_cast<const float4*>(Sm + col);
+    const float4* y4 = reinterpret_cast<const float4*>(Ym + col);
+    Accum<float> sg, yg, sy, yy;
+#pragma unroll
+    for (int m = 0; m < kLbPB; ++m) {
+      const int i = threadIdx.x + m * kChunkThreads;
+      if (i < nv) {
+        const float4 sv = s4[i], yv = y4[i];
+        add4(sg, sv, gv[m]);
+        add4(yg, yv, gv[m]);
+        add4(sy, sv, ynv[m]);
+        add4(yy, yv, ynv[m]);
+      }
+    }
+    const double v0 = warp_total(sg), v1 = warp_total(yg), v2 = warp_total(sy), v3 = warp_total(yy);
+    if (lane == 0) {
+      red[wid][4 * h + 0] = v0;
+      red[wid][4 * h + 1] = v1;
+      red[wid][4 * h + 2] = v2;
+      red[wid][4 * h + 3] = v3;
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < 4 * c; q += blockDim.x) {
+    double t = 0.0;
+    for (int w = 0; w < kChunkThreads / 32; ++w) t += red[w][q];
+    part[(size_t)blockIdx.x * 4 * RS + q] = t;
+  }
+}
+
+__global__ void __launch_bounds__(kChunkThreads) k_lb_dir_v4(LbArgs a, float* d, const float* g, const float* Sm,
+                                                             const float* Ym, double* part) {
+  __shared__ double red[40];
+  __shared__ float cf[2 * (kMaxHistory + 1)];
+  __shared__ int sl[kMaxHistory + 1];
+  const ChunkDev ch = a.chunks[blockIdx.x];
+  const LbfgsState S = a.st[ch.pair];
+  if (!S.active || S.phase != kLbDir) return;
+  const PairDev pr = a.pairs[ch.pair];
+  const int RS = a.MH + 1, c = S.hist_count, nv = ch.len >> 2;
+  if ((int)threadIdx.x < c) {
+    const int s_ = lb_age_slot(S, threadIdx.x, RS);
+    sl[threadIdx.x] = s_;
+    cf[2 * threadIdx.x] = (float)a.cs[(size_t)ch.pair * RS + s_];
+    cf[2 * threadIdx.x + 1] = (float)a.cy[(size_t)ch.pair * RS + s_];
+  }
+  __syncthreads();
+  const float mg = (float)(-S.gamma);
+  const float4* g4 = reinterpret_cast<const float4*>(g + pr.off + ch.start);
+  float4* d4 = reinterpret_cast<float4*>(d + pr.off + ch.start);
+  const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 gv[kLbPB], x[kLbPB];
+#pragma unroll
+  for (int m = 0; m < kLbPB; ++m) {
+    const int i = threadIdx.x + m * kChunkThreads;
+    gv[m] = i < nv ? g4[i] : z4;
+    x[m] = make_float4(mg * gv[m].x, mg * gv[m].y, mg * gv[m].z, mg * gv[m].w);
+  }
+  for (int h = 0; h < c; ++h) {
+    const long long col = pr.off * RS + (long long)sl[h] * pr.n + ch.start;
+    const float4* s4 = reinterpret_cast<const float4*>(Sm + col);
+    const float4* y4 = reinterpret_cast<const float4*>(Ym + col);
+    const float cs_ = cf[2 * h], cy_ = cf[2 * h + 1];
+#pragma unroll
+    for (int m = 0; m < kLbPB; ++m) {
+      const int i = threadIdx.x + m * kChunkThreads;
+      if (i < nv) {
+        const float4 sv = s4[i], yv = y4[i];
+        x[m].x = fmaf(cs_, sv.x, fmaf(cy_, yv.x, x[m].x));
+        x[m].y = fmaf(cs_, sv.y, fmaf(cy_, yv.y, x[m].y));
+        x[m].z = fmaf(cs_, sv.z, fmaf(cy_, yv.z, x[m].z));
+        x[m].w = fmaf(cs_, sv.w, fmaf(cy_, yv.w, x[m].w));
+      }
+    }
+  }
+  Accum<float> acc;
+#pragma unroll
+  for (int m = 0; m < kLbPB; ++m) {
+    const int i = threadIdx.x + m * kChunkThreads;
+    if (i < nv) {
+      d4[i] = x[m];
+      add4(acc, gv[m], x[m]);
+    }
+  }
+  const double tot = block_total<kChunkThreads>(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kChunkThreads) k_lb_trial_v4(LbArgs a, const int* search_mask, float* xt,
+                                                               const float* x, const float* d) {
+  const ChunkDev ch = a.chunks[blockIdx.x];
+  if (!search_mask[ch.pair]) return;
+  const PairDev pr = a.pairs[ch.pair];
+  const float t = (float)a.st[ch.pair].t;
+  const long long g0 = pr.off + ch.start;
+  const float4* x4 = reinterpret_cast<const float4*>(x + g0);
+  const float4* d4 = reinterpret_cast<const float4*>(d + g0);
+  float4* t4 = reinterpret_cast<float4*>(xt + g0);
+  for (int i = threadIdx.x; i < (ch.len >> 2); i += blockDim.x) {
+    const float4 xv = x4[i], dv = d4[i];
+    t4[i] = make_float4(fmaf(t, dv.x, xv.x), fmaf(t, dv.y, xv.y), fmaf(t, dv.z, xv.z), fmaf(t, dv.w, xv.w));
+  }
+}
+
+__global__ void __launch_bounds__(kChunkThreads) k_lb_accept_v4(LbArgs a, float* x, float* g, const float* xt,
+                                                                const float* gt, float* Sm, float* Ym) {
+  __shared__ double red[kChunkThreads / 32][4];
+  const ChunkDev ch = a.chunks[blockIdx.x];
+  const LbfgsState S = a.st[ch.pair];
+  if (!S.active || S.phase != kLbAccepted) return;
+  const PairDev pr = a.pairs[ch.pair];
+  const long long g0 = pr.off + ch.start;
+  const long long col = pr.off * (a.MH + 1) + (long long)S.hist_head * pr.n + ch.start;
+  float4* s4 = reinterpret_cast<float4*>(Sm + col);
+  float4* y4 = reinterpret_cast<float4*>(Ym + col);
+  float4* x4 = reinterpret_cast<float4*>(x + g0);
+  float4* g4 = reinterpret_cast<float4*>(g + g0);
+  const float4* xt4 = reinterpret_cast<const float4*>(xt + g0);
+  const float4* gt4 = reinterpret_cast<const float4*>(gt + g0);
+  Accum<float> sy, yy, ss, gg;
+  for (int i = threadIdx.x; i < (ch.len >> 2); i += blockDim.x) {
+    const float4 xn = xt4[i], gn = gt4[i], xo = x4[i], go = g4[i];
+    const float4 sv = make_float4(xn.x - xo.x, xn.y - xo.y, xn.z - xo.z, xn.w - xo.w);
+    const float4 yv = make_float4(gn.x - go.x, gn.y - go.y, gn.z - go.z, gn.w - go.w);
+    s4[i] = sv;
+    y4[i] = yv;
+    x4[i] = xn;
+    g4[i] = gn;
+    add4(sy, sv, yv);
+    add4(yy, yv, yv);
+    add4(ss, sv, sv);
+    add4(gg, gn, gn);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const double v0 = warp_total(sy), v1 = warp_total(yy), v2 = warp_total(ss), v3 = warp_total(gg);
+  if (lane == 0) {
+    red[wid][0] = v0;
+    red[wid][1] = v1;
+    red[wid][2] = v2;
+    red[wid][3] = v3;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double t = 0.0;
+    for (int w = 0; w < kChunkThreads / 32; ++w) t += red[w][threadIdx.x];
+    a.cpart[(size_t)blockIdx.x * 4 + threadIdx.x] = t;
+  }
+}
+
 // take the accepted steps (history, scaling, convergence test); count the pairs still running
 __global__ void k_lb_post(LbArgs a, int maxit, int* flag) {
   const int k = blockIdx.x;
   LbfgsState& S = a.st[k];
-  if (!S.active || threadIdx.x != 0) return;
+  if (!S.active) return;
   if (S.phase == kLbAccepted) {
     const PairDev pr = a.pairs[k];
     double v[4] = {0, 0, 0, 0};
-    for (int u = pr.cbeg; u < pr.cend; ++u)
+    for (int u = pr.cbeg + (int)threadIdx.x; u < pr.cend; u += 32)
       for (int c = 0; c < 4; ++c) v[c] += a.cpart[(size_t)u * 4 + c];
+    for (int c = 0; c < 4; ++c) v[c] = warp_sum(v[c]);
+    if (threadIdx.x != 0) return;
     const double sy = v[0], yy = v[1], ss = v[2], gg = v[3];
     if (sy > 1e-12 * sqrt(ss) * sqrt(yy)) {
       S.gamma = sy / yy;
@@ -327,7 +524,7 @@ __global__ void k_lb_post(LbArgs a, int maxit, int* flag) {
       S.status = BL_ENOCONV;
     }
   }
-  if (S.active) atomicAdd(flag, 1);
+  if (threadIdx.x == 0 && S.active) atomicAdd(flag, 1);
 }
 
 __global__ void k_lb_init(LbArgs a, const int* mask, const double* vals, const double* gn2, const double* ay2,
@@ -452,6 +649,8 @@ static bl_status lbfgs_impl(bl_problem* P, const std::vector<int>& mask_host, co
   double* ay2 = P->vals + 4 * K;       // K
   const double l2 = P->reg.l2_eps;
   const dim3 cg(P->n_chunks), ct(kChunkThreads);
+  // 128-bit vector passes for FP32 problems with 16-byte aligned columns
+  const bool v4 = sizeof(T) == 4 && P->vec4;
 
   // initial value and gradient; ||2 A y|| = ||grad Phi(0)|| for the relative tolerance
   st = launch_grad(P, x, g, mask, vals);
@@ -477,12 +676,20 @@ static bl_status lbfgs_impl(bl_problem* P, const std::vector<int>& mask_host, co
   auto body = [&]() -> bl_status {
     {
       ProfScope ps(P, BL_KC_LBFGS);
-      k_lb_dots<T><<<cg, ct, 0, P->stream>>>(a, g, Sm, Ym, P->cpart);
+      if (v4)
+        k_lb_dots_v4<<<cg, ct, 0, P->stream>>>(a, (const float*)(const void*)g, (const float*)(const void*)Sm,
+                                               (const float*)(const void*)Ym, P->cpart);
+      else
+        k_lb_dots<T><<<cg, ct, 0, P->stream>>>(a, g, Sm, Ym, P->cpart);
       BL_LAUNCH_CHECK(P);
       k_lb_compact<<<K, 32, 0, P->stream>>>(a, P->cpart);
       BL_LAUNCH_CHECK(P);
       double* pd = P->cpart + (size_t)P->n_chunks * 4 * (MH + 1);
-      k_lb_dir<T><<<cg, ct, 0, P->stream>>>(a, d, g, Sm, Ym, pd);
+      if (v4)
+        k_lb_dir_v4<<<cg, ct, 0, P->stream>>>(a, (float*)(void*)d, (const float*)(const void*)g,
+                                              (const float*)(const void*)Sm, (const float*)(const void*)Ym, pd);
+      else
+        k_lb_dir<T><<<cg, ct, 0, P->stream>>>(a, d, g, Sm, Ym, pd);
       BL_LAUNCH_CHECK(P);
       k_lb_gtd<<<K, 32, 0, P->stream>>>(a, pd);
       BL_LAUNCH_CHECK(P);
@@ -492,7 +699,11 @@ static bl_status lbfgs_impl(bl_problem* P, const std::vector<int>& mask_host, co
       BL_LAUNCH_CHECK(P);
       k_lb_begin_search<<<K, 32, 0, P->stream>>>(a, smask);
       BL_LAUNCH_CHECK(P);
-      k_lb_trial<T><<<cg, ct, 0, P->stream>>>(a, smask, xt, x, d);
+      if (v4)
+        k_lb_trial_v4<<<cg, ct, 0, P->stream>>>(a, smask, (float*)(void*)xt, (const float*)(const void*)x,
+                                                (const float*)(const void*)d);
+      else
+        k_lb_trial<T><<<cg, ct, 0, P->stream>>>(a, smask, xt, x, d);
       BL_LAUNCH_CHECK(P);
     }
     bl_status s2 = launch_grad(P, xt, gt, smask, vals);
@@ -500,7 +711,11 @@ static bl_status lbfgs_impl(bl_problem* P, const std::vector<int>& mask_host, co
     ProfScope ps(P, BL_KC_LBFGS);
     k_lb_armijo<<<K, 32, 0, P->stream>>>(a, smask, vals, l2, max_bt, o->armijo_slack, nullptr);
     BL_LAUNCH_CHECK(P);
-    k_lb_accept<T><<<cg, ct, 0, P->stream>>>(a, x, g, xt, gt, Sm, Ym);
+    if (v4)
+      k_lb_accept_v4<<<cg, ct, 0, P->stream>>>(a, (float*)(void*)x, (float*)(void*)g, (const float*)(const void*)xt,
+                                               (const float*)(const void*)gt, (float*)(void*)Sm, (float*)(void*)Ym);
+    else
+      k_lb_accept<T><<<cg, ct, 0, P->stream>>>(a, x, g, xt, gt, Sm, Ym);
     BL_LAUNCH_CHECK(P);
     BL_CUDA_TRY(cudaMemsetAsync(P->d_flag, 0, sizeof(int), P->stream));
     k_lb_post<<<K, 32, 0, P->stream>>>(a, o->max_iters, P->d_flag);
