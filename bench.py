@@ -59,6 +59,23 @@ FP32_LANES_PER_SM = 128
 # HBM copy bandwidth measured on the GB300s (STREAM-style copy), used when the driver's
 # MEASURED_PEAKS.json is absent from the working tree
 HBM_GBS_POOL = 6683.5
+# DRAM bytes (read + write) per pixel of one k_hvp_tma<5> launch, from an ncu capture of
+# dram__bytes_read.sum + dram__bytes_write.sum (first 16 pairs of the 64-pair batch, 1,306,624 px,
+# three launches: 68.1 B/px read each, the first writing 2.0 B/px back) scaled to the timed launches
+# by their pixels.  Valid while the kernel's sources hash to HVP_TRAFFIC_SHA; otherwise the roofline
+# reports null traffic.
+HVP_TRAFFIC_B_PER_PX = 70.1
+HVP_TRAFFIC_SOURCES = ("hvp_tma.cu", "device.cuh", "common.cuh")
+HVP_TRAFFIC_SHA = "c3ba9847d6bd4535"
+
+
+def hvp_traffic_valid():
+    import hashlib
+    h = hashlib.sha256()
+    for name in HVP_TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2412_08264_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16] == HVP_TRAFFIC_SHA
 
 
 def hvp_flops_per_pixel(n_filters, f, rb, masked=False):
@@ -724,14 +741,17 @@ def main():
     kvec = None
     if prof:
         hv = prof["hvp"]
+        traffic_ok = bool(rec["tma"]) and wl.filter_size == 5 and hvp_traffic_valid()
         n_l = max(1, hv["launches"])
         avg_ms, px = hv["ms"] / n_l, hv["pixels"] / n_l
         ach = fpp * px / (avg_ms * 1e-3) / 1e12 if avg_ms > 0 else None
         gbs = bpp * px / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else None
         roof.update({
             "achieved": ach, "frac": None if ach is None else ach / peak_tflops,
-            "traffic": None,
-            "traffic_source": "null: the kernel changed since its last ncu DRAM capture",
+            "traffic": (HVP_TRAFFIC_B_PER_PX * px if traffic_ok else None),
+            "traffic_source": (f"ncu dram__bytes_read.sum + dram__bytes_write.sum: {HVP_TRAFFIC_B_PER_PX} B/px "
+                               "on the first 16 pairs, times the pixels per timed launch" if traffic_ok else
+                               "null: the kernel changed since its last ncu DRAM capture"),
             "kernel": ("k_hvp_tma<5> (TMA-staged blur + FoE Hessian action)" if rec["tma"]
                        else "k_foe_stencil<float,5,HVP> (fused blur + FoE Hessian action + dots)"),
             "flops_per_pixel": fpp, "bytes_per_pixel": bpp, "pixels_per_launch": px, "avg_launch_ms": avg_ms,

@@ -345,10 +345,15 @@ __global__ void k_scalar1(KrylovArgs a, int use_tiles) {
   const int ncomp = use_tiles ? 1 + 2 * a.SMAX : 1 + 2 * a.SMAX;
   const double* part = use_tiles ? a.tpart : a.cpart;
   const int beg = use_tiles ? pr.tbeg : pr.cbeg, end = use_tiles ? pr.tend : pr.cend;
-  for (int m = threadIdx.x; m < 1 + s; m += blockDim.x) {
-    double t = 0.0;
-    for (int u = beg; u < end; ++u) t += part[(size_t)u * ncomp + m];
-    sh[m] = t;
+  {
+    // unit partials: a warp per value, its lanes over the pair's units
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int m = wid; m < 1 + s; m += nwarp) {
+      double t = 0.0;
+      for (int u = beg + lane; u < end; u += 32) t += part[(size_t)u * ncomp + m];
+      t = warp_sum(t);
+      if (lane == 0) sh[m] = t;
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -534,10 +539,14 @@ __global__ void k_scalar2(KrylovArgs a, int stop_nsc, int* flag) {
   const int s = a.s_k[k];
   const int nz = (stop_nsc && a.hasz[k]) ? s : 0;
   const int ncomp = 1 + a.SMAX;
-  for (int m = threadIdx.x; m <= nz; m += blockDim.x) {
-    double t = 0.0;
-    for (int u = pr.cbeg; u < pr.cend; ++u) t += a.cpart[(size_t)u * ncomp + m];
-    sh[m] = t;
+  {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int m = wid; m <= nz; m += nwarp) {
+      double t = 0.0;
+      for (int u = pr.cbeg + lane; u < pr.cend; u += 32) t += a.cpart[(size_t)u * ncomp + m];
+      t = warp_sum(t);
+      if (lane == 0) sh[m] = t;
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -672,10 +681,13 @@ __global__ void k_mr_scalar1(KrylovArgs a, int use_tiles, int nsc) {
   const int ncomp = 1 + 2 * a.SMAX;
   const double* part = use_tiles ? a.tpart : a.cpart;
   const int beg = use_tiles ? pr.tbeg : pr.cbeg, end = use_tiles ? pr.tend : pr.cend;
-  for (int m = threadIdx.x; m < 1 + s + nz; m += blockDim.x) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int m = wid; m < 1 + s + nz; m += nwarp) {
     const int slot = m <= s ? m : 1 + a.SMAX + (m - 1 - s);
     double t = 0.0;
-    for (int u = beg; u < end; ++u) t += part[(size_t)u * ncomp + slot];
+    for (int u = beg + lane; u < end; u += 32) t += part[(size_t)u * ncomp + slot];
+    t = warp_sum(t);
+    if (lane != 0) continue;
     if (m == 0) a.st[k].alpha = t;
     else if (m <= s) a.c[k * a.SMAX + m - 1] = t;
     else a.e[k * a.SMAX + m - 1 - s] = t;
@@ -718,9 +730,12 @@ __global__ void k_mr_scalar2(KrylovArgs a, int stop_nsc, int* flag) {
   const PairDev pr = a.pairs[k];
   const int s = a.s_k[k];
   const int nz = (stop_nsc && a.hasz[k]) ? s : 0;
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    for (int u = pr.cbeg + (int)threadIdx.x; u < pr.cend; u += 32) t += a.cpart[u];
+    t = warp_sum(t);
+  }
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int u = pr.cbeg; u < pr.cend; ++u) t += a.cpart[u];
     SolveState S = a.st[k];
     const double bn = sqrt(fmax(t, 0.0));
     const double gam = S.sm2 * S.beta_l;

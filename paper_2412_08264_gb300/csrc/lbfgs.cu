@@ -94,10 +94,13 @@ __global__ void k_lb_compact(LbArgs a, const double* part) {
   double* yy = a.yy + (size_t)k * RS * RS;
   double* cs = a.cs + (size_t)k * RS;
   double* cy = a.cy + (size_t)k * RS;
-  for (int q = threadIdx.x; q < 4 * c; q += blockDim.x) {
+  // chunk partials: a warp per value, its lanes over the pair's chunks
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int q = wid; q < 4 * c; q += nwarp) {
     double t = 0.0;
-    for (int un = pr.cbeg; un < pr.cend; ++un) t += part[(size_t)un * 4 * RS + q];
-    v[q] = t;
+    for (int un = pr.cbeg + lane; un < pr.cend; un += 32) t += part[(size_t)un * 4 * RS + q];
+    t = warp_sum(t);
+    if (lane == 0) v[q] = t;
   }
   for (int j = threadIdx.x; j < RS; j += blockDim.x) cs[j] = cy[j] = 0.0;
   for (int i = threadIdx.x; i < c; i += blockDim.x) sl[i] = lb_age_slot(S, i, RS);
@@ -682,7 +685,7 @@ static bl_status lbfgs_impl(bl_problem* P, const std::vector<int>& mask_host, co
       else
         k_lb_dots<T><<<cg, ct, 0, P->stream>>>(a, g, Sm, Ym, P->cpart);
       BL_LAUNCH_CHECK(P);
-      k_lb_compact<<<K, 32, 0, P->stream>>>(a, P->cpart);
+      k_lb_compact<<<K, 256, 0, P->stream>>>(a, P->cpart);
       BL_LAUNCH_CHECK(P);
       double* pd = P->cpart + (size_t)P->n_chunks * 4 * (MH + 1);
       if (v4)

@@ -135,9 +135,21 @@ __global__ void k_reduce_units(const PairDev* pairs, const double* part, int n_u
   const PairDev pr = pairs[k];
   const int beg = units == kUnitTiles ? pr.tbeg : units == kUnitJwTiles ? pr.jtbeg : units == kUnitHTiles ? pr.htbeg : pr.cbeg;
   const int end = units == kUnitTiles ? pr.tend : units == kUnitJwTiles ? pr.jtend : units == kUnitHTiles ? pr.htend : pr.cend;
+  const double* pc = part + (size_t)col * n_units * ncomp;
+  if (ncomp < 32) {
+    // few values: a warp per value, its lanes over the units
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int m = wid; m < ncomp; m += nwarp) {
+      double s = 0.0;
+      for (int u = beg + lane; u < end; u += 32) s += pc[(size_t)u * ncomp + m];
+      s = warp_sum(s);
+      if (lane == 0) out[((size_t)k * cols + col) * ncomp + m] = s;
+    }
+    return;
+  }
   for (int m = threadIdx.x; m < ncomp; m += blockDim.x) {
     double s = 0.0;
-    for (int u = beg; u < end; ++u) s += part[((size_t)col * n_units + u) * ncomp + m];
+    for (int u = beg; u < end; ++u) s += pc[(size_t)u * ncomp + m];
     out[((size_t)k * cols + col) * ncomp + m] = s;
   }
 }
