@@ -799,7 +799,8 @@ static bl_status refresh_impl(bl_problem* P, const std::vector<int>& mask_host, 
   // 4. selection
   {
     ProfScope ps(P, BL_KC_DENSE);
-    k_dense_select<<<K, 256, dsm, P->stream>>>(da);
+    // 16 warps: the Householder updates and the Jacobi rounds give a warp per column / per pair
+    k_dense_select<<<K, 512, dsm, P->stream>>>(da);
     BL_LAUNCH_CHECK(P);
   }
   // 5. U~ = W~ Y and Z = W~ Y2 in one pass over W~, C~ = HW~ Y
